@@ -1,0 +1,241 @@
+/*
+ * shm.h -- C ABI of the GB300 (sm_103a) Spherical Hermite Map library, libshm.so.
+ *
+ * Spherical Hermite Maps (Abouagour & Garyfallidis, arXiv 2602.20063) store, per texel of a
+ * padded cubemap, a radial function's value and scaled chart derivatives
+ * (r, r_u h, r_v h, r_uv h^2), h = 1/N (§3.3, Eq. hermite_storage), and reconstruct value and
+ * gradient together from a 2x2 texel footprint by bicubic Hermite interpolation (§3.3), from
+ * which the S^2 gradient and the surface normal follow (§3.4).
+ *
+ * Conventions (every entry point):
+ *   - All array pointers are DEVICE pointers owned by the caller, unless a comment says host.
+ *     The library allocates no device memory and keeps no state between calls.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *     The returned status covers host-side argument validation and launch errors only.
+ *   - Conditions found on the device never trap: they are OR-ed into *dev_status (device
+ *     int32, may be NULL) as SHM_DEV_* bits and the affected outputs are NaN.
+ *   - Directions need not be unit length; zero or non-finite directions give NaN outputs
+ *     and SHM_DEV_NONFINITE.
+ *   - Chart (paper §3.2 leaves it open): axis k = argmax |w_k| (ties -> lowest k),
+ *     face f = 2k + (w_k < 0), b_f = e_{(k+1)%3}, c_f = e_{(k+2)%3}, u = (w_{k+1}/|w_k| + 1)/2,
+ *     v = (w_{k+2}/|w_k| + 1)/2; texel centres u_i = (i - 1/2)/N for i = 0..N+1 (gutter at 0 and
+ *     N+1, §3.2).  Face table [f][j][i], channel innermost.
+ */
+#ifndef SHM_H
+#define SHM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* shm_stream; /* same type as cudaStream_t */
+
+typedef enum {
+    SHM_OK = 0,
+    SHM_ERR_INVALID_ARG = 1, /* a pointer, size or enum argument is invalid */
+    SHM_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. a dtype/layout pair) */
+    SHM_ERR_WORKSPACE = 3,   /* workspace missing or smaller than the *_workspace_bytes figure */
+    SHM_ERR_CUDA = 4,        /* a CUDA launch or runtime call failed */
+    SHM_ERR_TIMEOUT = 5      /* reserved for bounded device waits */
+} shm_status;
+
+/* Bits OR-ed into *dev_status by device code. */
+#define SHM_DEV_NONFINITE 1 /* zero / non-finite direction or non-finite coefficient met */
+#define SHM_DEV_BOUNDS 2    /* glyph / object index out of range; that item was skipped (NaN) */
+#define SHM_DEV_TIMEOUT 4   /* a bounded device wait gave up */
+
+typedef enum { SHM_F32 = 0, SHM_F16 = 1, SHM_BF16 = 2 } shm_dtype;
+
+/* Record layout of a table pool.
+ *   SHM_LAYOUT_TEXEL: one record per texel, [6][P][P] records per glyph, P = N+2 (the paper's
+ *                     RGBA face texture).  Record = 4 channels (16 B f32, 8 B 16-bit).
+ *   SHM_LAYOUT_CELL:  one record per interpolation cell, [6][N+1][N+1] records per glyph; a
+ *                     cell record holds its 2x2 corner texels (i,j),(i+1,j),(i,j+1),(i+1,j+1)
+ *                     back to back (64 B f32, 32 B 16-bit), so a query reads one aligned
+ *                     64 B / 32 B block.  Same values, 4x the bytes of the texel layout. */
+typedef enum { SHM_LAYOUT_TEXEL = 0, SHM_LAYOUT_CELL = 1 } shm_layout;
+
+/* A pool of per-glyph tables.  Represented radius = r0[g] + stored channel 0.
+ * If N_uniform > 0 every glyph has interior resolution N_uniform and glyph g starts at record
+ * g * shm_records_per_glyph(N_uniform, layout); N and offset may then be NULL.  Otherwise N[g]
+ * and offset[g] (in records of `layout`) describe glyph g. */
+typedef struct {
+    int32_t n_glyphs;
+    int32_t dtype;        /* shm_dtype */
+    int32_t layout;       /* shm_layout */
+    int32_t N_uniform;    /* > 0: uniform resolution; 0: per-glyph N[] / offset[] */
+    const int32_t* N;     /* device [n_glyphs] interior resolution, N >= 1 */
+    const int64_t* offset;/* device [n_glyphs] first record of each glyph */
+    const float* r0;      /* device [n_glyphs] value offset, or NULL (= 0) */
+    void* data;           /* device record pool, 16-byte aligned */
+} shm_lut;
+
+/* ---------------------------------------------------------------- sizes (host only) */
+
+/* Records one glyph of resolution N occupies in `layout`: 6(N+2)^2 or 6(N+1)^2. */
+int64_t shm_records_per_glyph(int32_t N, int32_t layout);
+
+/* Bytes of one record: 4 channels x 4 B (f32) or 2 B (16-bit), x 4 for the cell layout. */
+int64_t shm_record_bytes(int32_t dtype, int32_t layout);
+
+/* Host: fills offset_host[G] (records) for the per-glyph resolutions N_host[G] and returns
+ * the pool size in bytes in *bytes.  Either output may be NULL. */
+shm_status shm_lut_layout(int32_t G, const int32_t* N_host, int32_t dtype, int32_t layout,
+                          int64_t* offset_host, int64_t* bytes);
+
+/* ---------------------------------------------------------------- query (§3.2-§3.4) */
+
+/* Evaluates Q queries.  Query q reads direction dirs[q] (float32 [Q][3], AoS) on glyph
+ *   glyph[q]                       if glyph != NULL (int32 [Q]);
+ *   g with seg[g] <= q < seg[g+1]  if seg != NULL (int64 [n_glyphs+1], CSR, non-decreasing);
+ *   0                              otherwise.
+ * Per query (§3.2 chart and cell, §3.3 Hermite reconstruction and derivative extraction,
+ * §3.4 metric-tensor transport and normal):
+ *   R        = r0 + r(s,t)                                  -> R[q]            (float32 [Q])
+ *   R_u, R_v = (1/h) dr/ds, (1/h) dr/dt                     -> chart[2q..2q+1] (float32 [Q][2])
+ *   grad     = alpha e1 + beta e2 with G [alpha beta] = [R_u R_v] (§3.4) -> grad[3q..] ([Q][3])
+ *   normal   = (R w - grad) / |R w - grad|, w = d/|d|       -> normal[3q..]    ([Q][3])
+ *   fij      = (face, i, j) of the 2x2 footprint            -> fij[3q..]       (int32 [Q][3])
+ * Any output pointer may be NULL to skip it.  Inputs are read-only; outputs are overwritten.
+ * Returns SHM_ERR_INVALID_ARG for a NULL lut/dirs, Q < 0, or an invalid dtype/layout. */
+shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
+                     const int64_t* seg, float* R, float* grad, float* normal, float* chart,
+                     int32_t* fij, int32_t* dev_status, shm_stream stream);
+
+/* ---------------------------------------------------------------- bake (Algorithm 1) */
+
+typedef enum {
+    SHM_SRC_SH = 0,      /* real SH coefficients; analytic derivatives (§3.3) */
+    SHM_SRC_SAMPLES = 1, /* sampled values on a margin grid; central differences (§3.3) */
+    SHM_SRC_BUMPS = 2,   /* R = 1 + sum_k a_k exp(-|w - mu_k|^2 / (2 w_k^2)), central differences */
+    SHM_SRC_FBM = 3      /* h = amplitude * fBm(value noise), central differences (§4.10) */
+} shm_source_kind;
+
+/* Source of a bake.  All arrays device.
+ *   SH:      coeffs [G][(L+1)^2] float32, index l*l + l + m (orthonormal real SH, no
+ *            Condon-Shortley phase); basis from shm_sh_basis for (N_uniform, L).  SH sources
+ *            need a uniform-N pool.
+ *   SAMPLES: samples float32, glyph g's grid [6][N+4][N+4] at sample_offset[g] (floats);
+ *            grid entry (jj, ii) is the value at texel centre (ii-1, jj-1) (one-texel bake
+ *            margin around the padded face, §3.3).
+ *   BUMPS:   bump_offset [G+1] (CSR), mu [B][3] unit vectors, amp [B], width [B] (radians).
+ *   FBM:     keys [octaves][3] uint32 lattice keys; R = r0 + amplitude * sum_o gain^o
+ *            noise(w base_freq lacunarity^o) (PCG3D-hashed value noise, quintic fade).
+ * The stored channel 0 is the function minus r0[g] (r0 may be NULL = 0). */
+typedef struct {
+    int32_t kind;
+    int32_t L;
+    const float* coeffs;
+    const float* basis;
+    const float* samples;
+    const int64_t* sample_offset;
+    const int64_t* bump_offset;
+    const float* mu;
+    const float* amp;
+    const float* width;
+    int32_t octaves;
+    const uint32_t* keys;
+    float base_freq, lacunarity, gain, amplitude;
+} shm_source;
+
+/* Bytes of the SH bake basis for resolution N and degree L (host). */
+int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
+
+/* Fills `basis` (device, shm_sh_basis_bytes) with every real SH function's record
+ * (Y, Y_u h, Y_v h, Y_uv h^2) at every stored texel of the padded cubemap, from analytic
+ * derivatives converted to the chart by the chain rule (§3.3, Algorithm 1).  The bake of
+ * coefficients c is then lut = sum_k c_k basis_k.  Compute once per (N, L) and reuse. */
+shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream);
+
+/* Writes every record of every glyph of `lut` (any dtype/layout) from `src` (Algorithm 1:
+ * gutter texels evaluated at their own centres, derivative channels in each face's chart).
+ * ws/ws_bytes: workspace, may be NULL/0 (no current source needs one). */
+shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, size_t ws_bytes,
+                         shm_stream stream);
+
+/* Re-encodes table `src` into `dst` (same glyphs and resolutions; any dtype/layout pair).
+ * 16-bit stores round to nearest even.  dst channel 0 = src r0 + src channel 0 - dst r0. */
+shm_status shm_pack_lut(const shm_lut* src, const shm_lut* dst, shm_stream stream);
+
+/* Per-glyph bound R_max >= |r0 + interpolated r| over the sphere (for ray bracketing, §3.1):
+ * max|r0 + r| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16 over the glyph's texels.
+ * rmax: device float32 [n_glyphs]. */
+shm_status shm_lut_bounds(const shm_lut* lut, float* rmax, shm_stream stream);
+
+/* ---------------------------------------------------------------- adjoint (not in the paper) */
+
+/* Reverse mode of shm_query.  Upstream gradients gR [Q], ggrad [Q][3], gnormal [Q][3] (each
+ * may be NULL = 0).  Accumulates (+=) dL/d(stored record) into dlut, a float32 TEXEL-layout
+ * table with the same glyphs and resolutions as lut (any lut dtype/layout is read), and
+ * writes (=) dL/d(dirs) into ddirs [Q][3] if not NULL.  Atomic accumulation: the summation
+ * order, hence the last bits of dlut, may vary from run to run. */
+shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
+                              const int32_t* glyph, const int64_t* seg, const float* gR,
+                              const float* ggrad, const float* gnormal, const shm_lut* dlut,
+                              float* ddirs, int32_t* dev_status, shm_stream stream);
+
+/* Reverse mode of the SH bake: dcoeffs[g][k] (=) sum over texels and channels of
+ * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L). */
+shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis,
+                                  float* dcoeffs, shm_stream stream);
+
+/* ---------------------------------------------------------------- direct SH (ground truth) */
+
+/* Direct evaluation of r(w) = sum c_lm Y_lm(w) with its S^2 gradient and normal (no table),
+ * same glyph selection as shm_query.  coeffs [G][(L+1)^2] float32. */
+shm_status shm_sh_eval(int32_t L, int32_t n_glyphs, const float* coeffs, int64_t Q,
+                       const float* dirs, const int32_t* glyph, const int64_t* seg, float* R,
+                       float* grad, float* normal, int32_t* dev_status, shm_stream stream);
+
+/* ---------------------------------------------------------------- ray casting (§3.1) */
+
+typedef struct {
+    float eye[3], fwd[3], right[3], up[3]; /* orthonormal camera frame */
+    float tan_half_fov_y;
+    int32_t W, H;
+} shm_camera;
+
+typedef struct {
+    int32_t march;  /* uniform F samples over the bounding-sphere chord (>= 1) */
+    int32_t bisect; /* bisection steps after the first sign change */
+    int32_t newton; /* Newton-Raphson steps after bisection */
+    float ambient, kd, ks, shininess;
+    float light[3];
+} shm_raycast_params;
+
+typedef struct {
+    float centre[3];
+    float scale;  /* s > 0: R = s |r| */
+    float rmax;   /* bounding-sphere radius (scale * shm_lut_bounds) */
+    int32_t glyph;
+} shm_object;
+
+/* Workspace bytes shm_raycast needs for n_obj objects on a W x H image (host). */
+int64_t shm_raycast_workspace_bytes(int32_t n_obj, int32_t W, int32_t H);
+
+/* Ray casts star-shaped objects x(w) = c + s|r(w)| w (§3.1): per pixel ray p(t) = o + t d
+ * with d = normalise(fwd + x_ndc tan(fov/2)(W/H) right + y_ndc tan(fov/2) up),
+ * x_ndc = 2(px+1/2)/W - 1, y_ndc = 1 - 2(py+1/2)/H; per object the bounding-sphere chord
+ * [t_min, t_max] is sampled `march` times, the first sample with F < 0 brackets the root of
+ * F(x) = |x - c| - R(w), which is refined by `bisect` bisection and `newton` Newton steps;
+ * the nearest hit is shaded Blinn-Phong with the analytic normal (§3.4, signed rule
+ * grad R = s sign(r) grad r).  Outputs (row-major, may be NULL): rgba [H][W][4],
+ * depth [H][W] (t, +inf on a miss), normal [H][W][3], obj_id [H][W] (-1 on a miss).
+ * objs: device [n_obj]; cam, prm: HOST structs. */
+shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj,
+                       const shm_camera* cam, const shm_raycast_params* prm, float* rgba,
+                       float* depth, float* normal, int32_t* obj_id, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, shm_stream stream);
+
+/* ---------------------------------------------------------------- misc */
+
+const char* shm_status_string(shm_status s);
+int32_t shm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHM_H */

@@ -368,3 +368,24 @@ def raycast(pool, off, Ns, centre, scale, rmax, glyph, cam, prm, px=None, py=Non
                              _p(out["depth"], _d), _p(out["normal"], _d), _p(out["obj_id"], _i32),
                              _p(out["margin"], _d), C.c_int(nthreads or nthreads_default()))
     return out
+
+
+# ----------------------------------------------------------------- storage quantisation
+def quantize_f16(x32):
+    """float32 -> float16 -> float64, round to nearest even (IEEE conversion)."""
+    return np.asarray(x32, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+def quantize_bf16(x32):
+    """float32 -> bfloat16 (round to nearest even on the top 16 bits) -> float64."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    nan = np.isnan(np.asarray(x32, dtype=np.float32))
+    out = (rounded.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+def bf16_bits(x32):
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)

@@ -106,20 +106,29 @@ void shmo_sample_grid_fbm(int N, int octaves, const uint32_t* keys, double base_
             }
 }
 
-/* Upper bound of |interpolated r| over the sphere for one glyph table: the value weights are
- * non-negative and sum to 1 per axis, and sum_a |H^d_a(s)| = s(1-s) <= 1/4, so
- * |r| <= max|r0 + r_ab| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16.  Used as the
- * bounding-sphere radius R_max of §3.1. */
+/* Upper bound of |interpolated r| over the sphere for one glyph table.  On one cell the value
+ * weights H_a(s)H_b(t) are non-negative and sum to 1, and sum_a |H^d_a(s)| = s(1-s) <= 1/4, so
+ * |r| <= max|r0 + r_ab| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16 with the maxima over the
+ * cell's four corners; the bound is the largest such cell bound.  Used as the bounding-sphere
+ * radius R_max of §3.1 (the paper says only "a bounding sphere"). */
 double shmo_lut_bound(const double* glut, int N, double r0)
 {
-    size_t T = (size_t)6 * (N + 2) * (N + 2);
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
-    for (size_t t = 0; t < T; ++t) {
-        const double* p = glut + 4 * t;
-        if (fabs(r0 + p[0]) > m0) m0 = fabs(r0 + p[0]);
-        if (fabs(p[1]) > m1) m1 = fabs(p[1]);
-        if (fabs(p[2]) > m2) m2 = fabs(p[2]);
-        if (fabs(p[3]) > m3) m3 = fabs(p[3]);
-    }
-    return m0 + (m1 + m2) / 4.0 + m3 / 16.0;
+    int P = N + 2;
+    double best = 0.0;
+    for (int f = 0; f < 6; ++f)
+        for (int j = 0; j <= N; ++j)
+            for (int i = 0; i <= N; ++i) {
+                double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+                for (int b = 0; b < 2; ++b)
+                    for (int a = 0; a < 2; ++a) {
+                        const double* p = glut + (((size_t)f * P + (j + b)) * P + (i + a)) * 4;
+                        if (fabs(r0 + p[0]) > m0) m0 = fabs(r0 + p[0]);
+                        if (fabs(p[1]) > m1) m1 = fabs(p[1]);
+                        if (fabs(p[2]) > m2) m2 = fabs(p[2]);
+                        if (fabs(p[3]) > m3) m3 = fabs(p[3]);
+                    }
+                double cb = m0 + (m1 + m2) / 4.0 + m3 / 16.0;
+                if (cb > best) best = cb;
+            }
+    return best;
 }

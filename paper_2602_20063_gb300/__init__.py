@@ -1,0 +1,15 @@
+"""GB300 (sm_103a) Spherical Hermite Maps: batched evaluation of star-shaped radial functions
+through padded cubemap Hermite tables (Abouagour & Garyfallidis, arXiv 2602.20063).
+
+The compute lives in libshm.so (CUDA, C ABI in include/shm.h); this package is its thin
+binding plus the autograd wrapper.  See ``binding`` for the entry points.
+"""
+from .binding import (  # noqa: F401
+    SHM_F32, SHM_F16, SHM_BF16, SHM_LAYOUT_TEXEL, SHM_LAYOUT_CELL,
+    SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM,
+    SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT,
+    Lut, Source, ShmError, alloc_lut, like_lut, lib, lib_path,
+    query, sh_basis, build_lut, pack_lut, lut_bounds, query_backward, build_lut_backward, sh_eval,
+    make_camera, make_raycast_params, objects_tensor, raycast, raycast_workspace_bytes, raycast_query_count,
+    records_per_glyph, record_bytes,
+)

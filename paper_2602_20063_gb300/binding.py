@@ -1,0 +1,393 @@
+"""Thin Python binding of libshm.so (include/shm.h): the same entry points, argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch only provides device memory and the current
+stream.  Importing this module does not load the library; the first call does, and raises
+``RuntimeError`` if libshm.so has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``).  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+SHM_F32, SHM_F16, SHM_BF16 = 0, 1, 2
+SHM_LAYOUT_TEXEL, SHM_LAYOUT_CELL = 0, 1
+SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM = 0, 1, 2, 3
+SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT = 1, 2, 4
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error", 5: "timeout"}
+
+DTYPES = {SHM_F32: torch.float32, SHM_F16: torch.float16, SHM_BF16: torch.bfloat16}
+DTYPE_NAMES = {"f32": SHM_F32, "f16": SHM_F16, "bf16": SHM_BF16}
+LAYOUT_NAMES = {"texel": SHM_LAYOUT_TEXEL, "cell": SHM_LAYOUT_CELL}
+
+
+class ShmError(RuntimeError):
+    pass
+
+
+class c_lut(C.Structure):
+    _fields_ = [("n_glyphs", C.c_int32), ("dtype", C.c_int32), ("layout", C.c_int32), ("N_uniform", C.c_int32),
+                ("N", C.c_void_p), ("offset", C.c_void_p), ("r0", C.c_void_p), ("data", C.c_void_p)]
+
+
+class c_source(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("L", C.c_int32), ("coeffs", C.c_void_p), ("basis", C.c_void_p),
+                ("samples", C.c_void_p), ("sample_offset", C.c_void_p), ("bump_offset", C.c_void_p),
+                ("mu", C.c_void_p), ("amp", C.c_void_p), ("width", C.c_void_p), ("octaves", C.c_int32),
+                ("keys", C.c_void_p), ("base_freq", C.c_float), ("lacunarity", C.c_float), ("gain", C.c_float),
+                ("amplitude", C.c_float)]
+
+
+class c_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("fwd", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3),
+                ("tan_half_fov_y", C.c_float), ("W", C.c_int32), ("H", C.c_int32)]
+
+
+class c_raycast_params(C.Structure):
+    _fields_ = [("march", C.c_int32), ("bisect", C.c_int32), ("newton", C.c_int32), ("ambient", C.c_float),
+                ("kd", C.c_float), ("ks", C.c_float), ("shininess", C.c_float), ("light", C.c_float * 3)]
+
+
+class c_object(C.Structure):
+    _fields_ = [("centre", C.c_float * 3), ("scale", C.c_float), ("rmax", C.c_float), ("glyph", C.c_int32)]
+
+
+_lib = None
+
+_VP, _I32, _I64, _SZ = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+_SIGS = {
+    "shm_records_per_glyph": (C.c_int64, [_I32, _I32]),
+    "shm_record_bytes": (C.c_int64, [_I32, _I32]),
+    "shm_lut_layout": (C.c_int, [_I32, _VP, _I32, _I32, _VP, _VP]),
+    "shm_query": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_sh_basis_bytes": (C.c_int64, [_I32, _I32]),
+    "shm_sh_basis": (C.c_int, [_I32, _I32, _VP, _VP]),
+    "shm_build_lut": (C.c_int, [_VP, _VP, _VP, _SZ, _VP]),
+    "shm_pack_lut": (C.c_int, [_VP, _VP, _VP]),
+    "shm_lut_bounds": (C.c_int, [_VP, _VP, _VP]),
+    "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "shm_sh_eval": (C.c_int, [_I32, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_raycast_workspace_bytes": (C.c_int64, [_I32, _I32, _I32]),
+    "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "shm_status_string": (C.c_char_p, [C.c_int]),
+    "shm_version": (C.c_int32, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libshm.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libshm.so not found at {path}: build it with paper_2602_20063_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise ShmError(f"{what}: {lib().shm_status_string(st).decode()} (status {st})")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need(t: Optional[torch.Tensor], dtype, shape=None, name="tensor"):
+    if t is None:
+        return
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+# ------------------------------------------------------------------------------------------- tables
+def records_per_glyph(N: int, layout: int) -> int:
+    return int(lib().shm_records_per_glyph(int(N), int(layout)))
+
+
+def record_bytes(dtype: int, layout: int) -> int:
+    return int(lib().shm_record_bytes(int(dtype), int(layout)))
+
+
+def records_per_glyph_host(N: int, layout: int) -> int:
+    P = N + 1 if layout == SHM_LAYOUT_CELL else N + 2
+    return 6 * P * P
+
+
+@dataclass
+class Lut:
+    """A pool of per-glyph tables on the device (see shm_lut in include/shm.h)."""
+    data: torch.Tensor
+    n_glyphs: int
+    dtype: int = SHM_F32
+    layout: int = SHM_LAYOUT_TEXEL
+    N_uniform: int = 0
+    N: Optional[torch.Tensor] = None       # int32 [G]
+    offset: Optional[torch.Tensor] = None  # int64 [G]
+    r0: Optional[torch.Tensor] = None      # float32 [G]
+    _c: c_lut = field(default=None, repr=False)
+
+    def c(self) -> c_lut:
+        s = c_lut()
+        s.n_glyphs, s.dtype, s.layout, s.N_uniform = self.n_glyphs, self.dtype, self.layout, self.N_uniform
+        s.N = self.N.data_ptr() if self.N is not None else None
+        s.offset = self.offset.data_ptr() if self.offset is not None else None
+        s.r0 = self.r0.data_ptr() if self.r0 is not None else None
+        s.data = self.data.data_ptr()
+        self._c = s
+        return s
+
+    def glyph_N(self, g: int) -> int:
+        return self.N_uniform if self.N_uniform > 0 else int(self.N[g])
+
+
+def alloc_lut(n_glyphs: int, N, dtype: int = SHM_F32, layout: int = SHM_LAYOUT_TEXEL, r0=None, device="cuda",
+              zero: bool = False) -> Lut:
+    """Allocate a table pool: N is an int (uniform) or a sequence of per-glyph resolutions."""
+    rb = 16 if dtype == SHM_F32 else 8
+    if layout == SHM_LAYOUT_CELL:
+        rb *= 4
+    elem = 4 if dtype == SHM_F32 else 2
+    if isinstance(N, int):
+        Ns = None
+        total = n_glyphs * records_per_glyph_host(N, layout)
+        N_uniform, Nt, Ot = N, None, None
+    else:
+        Ns = [int(n) for n in N]
+        assert len(Ns) == n_glyphs
+        offs, total = [], 0
+        for n in Ns:
+            offs.append(total)
+            total += records_per_glyph_host(n, layout)
+        N_uniform = 0
+        Nt = torch.tensor(Ns, dtype=torch.int32, device=device)
+        Ot = torch.tensor(offs, dtype=torch.int64, device=device)
+    n_elem = total * rb // elem
+    alloc = torch.zeros if zero else torch.empty
+    data = alloc(n_elem, dtype=DTYPES[dtype], device=device)
+    r0t = None
+    if r0 is not None:
+        r0t = torch.as_tensor(r0, dtype=torch.float32, device=device).reshape(-1).contiguous()
+        if r0t.numel() == 1 and n_glyphs > 1:
+            r0t = r0t.expand(n_glyphs).contiguous()
+    return Lut(data=data, n_glyphs=n_glyphs, dtype=dtype, layout=layout, N_uniform=N_uniform, N=Nt, offset=Ot, r0=r0t)
+
+
+def like_lut(L: Lut, dtype: int = None, layout: int = None, r0="same", zero=False) -> Lut:
+    """A table with L's glyphs and resolutions in another dtype/layout."""
+    dtype = L.dtype if dtype is None else dtype
+    layout = L.layout if layout is None else layout
+    if L.N_uniform > 0:
+        N = L.N_uniform
+    else:
+        N = [int(n) for n in L.N.tolist()]
+    rr = (L.r0 if r0 == "same" else r0)
+    out = alloc_lut(L.n_glyphs, N, dtype, layout, r0=None, device=L.data.device, zero=zero)
+    if rr is not None:
+        out.r0 = torch.as_tensor(rr, dtype=torch.float32, device=L.data.device).reshape(-1).contiguous()
+    return out
+
+
+# ------------------------------------------------------------------------------------------- query
+def query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.Tensor = None,
+          want=("R", "grad", "normal"), out: dict = None, dev_status: torch.Tensor = None, stream=None) -> dict:
+    """shm_query: returns a dict of the requested outputs among R, grad, normal, chart, fij."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    _need(glyph, torch.int32, (Q,), "glyph")
+    _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
+    dev = dirs.device
+    out = {} if out is None else out
+    shapes = {"R": (Q,), "grad": (Q, 3), "normal": (Q, 3), "chart": (Q, 2), "fij": (Q, 3)}
+    for k in want:
+        if k not in out:
+            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "fij" else torch.float32, device=dev)
+    st = lib().shm_query(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(out.get("R")),
+                         _ptr(out.get("grad")), _ptr(out.get("normal")), _ptr(out.get("chart")),
+                         _ptr(out.get("fij")), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_query")
+    return out
+
+
+# ------------------------------------------------------------------------------------------- bake
+def sh_basis(N: int, L: int, device="cuda", stream=None) -> torch.Tensor:
+    nbytes = int(lib().shm_sh_basis_bytes(N, L))
+    if nbytes < 0:
+        raise ShmError("shm_sh_basis_bytes: invalid N/L")
+    B = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+    _check(lib().shm_sh_basis(N, L, _ptr(B), _stream(stream)), "shm_sh_basis")
+    return B
+
+
+@dataclass
+class Source:
+    kind: int
+    L: int = 0
+    coeffs: torch.Tensor = None
+    basis: torch.Tensor = None
+    samples: torch.Tensor = None
+    sample_offset: torch.Tensor = None
+    bump_offset: torch.Tensor = None
+    mu: torch.Tensor = None
+    amp: torch.Tensor = None
+    width: torch.Tensor = None
+    octaves: int = 0
+    keys: torch.Tensor = None
+    base_freq: float = 2.0
+    lacunarity: float = 2.0
+    gain: float = 0.5
+    amplitude: float = 0.02
+
+    def c(self) -> c_source:
+        s = c_source()
+        s.kind, s.L, s.octaves = self.kind, self.L, self.octaves
+        for name in ("coeffs", "basis", "samples", "sample_offset", "bump_offset", "mu", "amp", "width", "keys"):
+            t = getattr(self, name)
+            setattr(s, name, t.data_ptr() if t is not None else None)
+        s.base_freq, s.lacunarity, s.gain, s.amplitude = self.base_freq, self.lacunarity, self.gain, self.amplitude
+        return s
+
+
+def build_lut(lut: Lut, src: Source, stream=None):
+    _check(lib().shm_build_lut(C.byref(lut.c()), C.byref(src.c()), None, 0, _stream(stream)), "shm_build_lut")
+
+
+def pack_lut(src: Lut, dst: Lut, stream=None):
+    _check(lib().shm_pack_lut(C.byref(src.c()), C.byref(dst.c()), _stream(stream)), "shm_pack_lut")
+
+
+def lut_bounds(lut: Lut, stream=None) -> torch.Tensor:
+    r = torch.empty(lut.n_glyphs, dtype=torch.float32, device=lut.data.device)
+    _check(lib().shm_lut_bounds(C.byref(lut.c()), _ptr(r), _stream(stream)), "shm_lut_bounds")
+    return r
+
+
+# ------------------------------------------------------------------------------------------- adjoint
+def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None, gnormal=None, glyph=None, seg=None,
+                   want_ddirs=True, dev_status=None, stream=None):
+    """shm_query_backward: accumulates into dlut (float32 texel layout); returns ddirs or None."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    for t, nm in ((gR, "gR"), (ggrad, "ggrad"), (gnormal, "gnormal")):
+        _need(t, torch.float32, name=nm)
+    ddirs = torch.empty((Q, 3), dtype=torch.float32, device=dirs.device) if want_ddirs else None
+    st = lib().shm_query_backward(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(gR), _ptr(ggrad),
+                                  _ptr(gnormal), C.byref(dlut.c()), _ptr(ddirs), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_query_backward")
+    return ddirs
+
+
+def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None) -> torch.Tensor:
+    K = (L + 1) ** 2
+    dc = torch.empty((dlut.n_glyphs, K), dtype=torch.float32, device=dlut.data.device)
+    _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc), _stream(stream)),
+           "shm_build_lut_backward")
+    return dc
+
+
+# ------------------------------------------------------------------------------------------- direct SH
+def sh_eval(L: int, coeffs: torch.Tensor, dirs: torch.Tensor, glyph=None, seg=None, dev_status=None, stream=None):
+    _need(coeffs, torch.float32, name="coeffs")
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    G = coeffs.shape[0]
+    R = torch.empty(Q, dtype=torch.float32, device=dirs.device)
+    grad = torch.empty((Q, 3), dtype=torch.float32, device=dirs.device)
+    normal = torch.empty((Q, 3), dtype=torch.float32, device=dirs.device)
+    st = lib().shm_sh_eval(L, G, _ptr(coeffs), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(R), _ptr(grad),
+                           _ptr(normal), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_sh_eval")
+    return R, grad, normal
+
+
+# ------------------------------------------------------------------------------------------- raycast
+def make_camera(eye, fwd, right, up, fov_y_deg: float, W: int, H: int) -> c_camera:
+    import math
+    cam = c_camera()
+    for q in range(3):
+        cam.eye[q], cam.fwd[q], cam.right[q], cam.up[q] = eye[q], fwd[q], right[q], up[q]
+    cam.tan_half_fov_y = math.tan(math.radians(fov_y_deg) / 2.0)
+    cam.W, cam.H = int(W), int(H)
+    return cam
+
+
+def make_raycast_params(march=32, bisect=12, newton=3, ambient=0.1, kd=0.7, ks=0.3, shininess=64.0,
+                        light=(1.0, 1.0, 1.0)) -> c_raycast_params:
+    p = c_raycast_params()
+    p.march, p.bisect, p.newton = march, bisect, newton
+    p.ambient, p.kd, p.ks, p.shininess = ambient, kd, ks, shininess
+    for q in range(3):
+        p.light[q] = light[q]
+    return p
+
+
+def objects_tensor(centre, scale, rmax, glyph, device="cuda") -> torch.Tensor:
+    """Pack object records (shm_object, 24 B each) into a device byte tensor."""
+    import numpy as np
+    n = len(scale)
+    rec = np.zeros(n, dtype=[("c", "<f4", 3), ("s", "<f4"), ("r", "<f4"), ("g", "<i4")])
+    rec["c"] = np.asarray(centre, dtype=np.float32).reshape(n, 3)
+    rec["s"] = np.asarray(scale, dtype=np.float32)
+    rec["r"] = np.asarray(rmax, dtype=np.float32)
+    rec["g"] = np.asarray(glyph, dtype=np.int32)
+    return torch.from_numpy(rec.view(np.uint8).copy()).to(device)
+
+
+def raycast_workspace_bytes(n_obj: int, W: int, H: int) -> int:
+    return int(lib().shm_raycast_workspace_bytes(n_obj, W, H))
+
+
+def raycast(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm: c_raycast_params, ws: torch.Tensor = None,
+            want=("rgba", "depth", "normal", "obj_id"), out: dict = None, dev_status=None, stream=None) -> dict:
+    W, H = cam.W, cam.H
+    dev = lut.data.device
+    nb = raycast_workspace_bytes(n_obj, W, H)
+    if ws is None:
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    out = {} if out is None else out
+    shapes = {"rgba": (H, W, 4), "depth": (H, W), "normal": (H, W, 3), "obj_id": (H, W)}
+    for k in want:
+        if k not in out:
+            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "obj_id" else torch.float32, device=dev)
+    st = lib().shm_raycast(C.byref(lut.c()), _ptr(objs), n_obj, C.byref(cam), C.byref(prm), _ptr(out.get("rgba")),
+                           _ptr(out.get("depth")), _ptr(out.get("normal")), _ptr(out.get("obj_id")), _ptr(ws),
+                           ws.numel(), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_raycast")
+    out["_ws"] = ws
+    return out
+
+
+def raycast_query_count(ws: torch.Tensor) -> int:
+    """Surface queries the last shm_raycast on this workspace evaluated (workspace header)."""
+    return int(ws[8:16].view(torch.int64).item())

@@ -1,0 +1,288 @@
+// C-ABI entry points of libshm.so (declared in include/shm.h): host-side validation, dispatch
+// to the kernel launchers, CUDA error mapping.  No device memory is allocated here.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "shm_internal.h"
+
+namespace shm {
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cached[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+static bool valid_dtype(int d) { return d == SHM_F32 || d == SHM_F16 || d == SHM_BF16; }
+static bool valid_layout(int l) { return l == SHM_LAYOUT_TEXEL || l == SHM_LAYOUT_CELL; }
+
+static shm_status check_lut(const shm_lut* L)
+{
+    if (!L || !L->data || L->n_glyphs <= 0) return SHM_ERR_INVALID_ARG;
+    if (!valid_dtype(L->dtype) || !valid_layout(L->layout)) return SHM_ERR_INVALID_ARG;
+    if (L->N_uniform < 0) return SHM_ERR_INVALID_ARG;
+    if (L->N_uniform == 0 && (!L->N || !L->offset)) return SHM_ERR_INVALID_ARG;
+    if (L->N_uniform > (1 << 20)) return SHM_ERR_INVALID_ARG;
+    if (((uintptr_t)L->data & 15u) != 0) return SHM_ERR_INVALID_ARG;
+    return SHM_OK;
+}
+
+static LutView view(const shm_lut* L)
+{
+    LutView v;
+    v.data = L->data;
+    v.N = L->N;
+    v.offset = L->offset;
+    v.r0 = L->r0;
+    v.n_glyphs = L->n_glyphs;
+    v.N_uniform = L->N_uniform;
+    v.dtype = L->dtype;
+    v.layout = L->layout;
+    return v;
+}
+
+static shm_status map_cuda(cudaError_t e) { return e == cudaSuccess ? SHM_OK : SHM_ERR_CUDA; }
+
+// Largest per-glyph N: uniform N, or read from the device array (one small synchronous copy
+// on `stream`; callers with N_uniform avoid it).
+static int max_N_of(const shm_lut* L, cudaStream_t s, shm_status* st)
+{
+    *st = SHM_OK;
+    if (L->N_uniform > 0) return L->N_uniform;
+    int mx = 0;
+    const int G = L->n_glyphs;
+    int32_t buf[1024];
+    for (int g0 = 0; g0 < G; g0 += 1024) {
+        const int n = G - g0 < 1024 ? G - g0 : 1024;
+        if (cudaMemcpyAsync(buf, L->N + g0, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            *st = SHM_ERR_CUDA;
+            return 0;
+        }
+        for (int q = 0; q < n; ++q) {
+            if (buf[q] < 1 || buf[q] > (1 << 20)) { *st = SHM_ERR_INVALID_ARG; return 0; }
+            if (buf[q] > mx) mx = buf[q];
+        }
+    }
+    return mx;
+}
+
+}  // namespace shm
+
+using namespace shm;
+
+extern "C" {
+
+int64_t shm_records_per_glyph(int32_t N, int32_t layout)
+{
+    if (N < 1 || !valid_layout(layout)) return -1;
+    return records_per_glyph(N, layout);
+}
+
+int64_t shm_record_bytes(int32_t dtype, int32_t layout)
+{
+    if (!valid_dtype(dtype) || !valid_layout(layout)) return -1;
+    const int64_t b = (dtype == SHM_F32) ? 16 : 8;
+    return layout == SHM_LAYOUT_CELL ? 4 * b : b;
+}
+
+shm_status shm_lut_layout(int32_t G, const int32_t* N_host, int32_t dtype, int32_t layout, int64_t* offset_host,
+                          int64_t* bytes)
+{
+    if (G <= 0 || !N_host || !valid_dtype(dtype) || !valid_layout(layout)) return SHM_ERR_INVALID_ARG;
+    int64_t off = 0;
+    for (int g = 0; g < G; ++g) {
+        if (N_host[g] < 1 || N_host[g] > (1 << 20)) return SHM_ERR_INVALID_ARG;
+        if (offset_host) offset_host[g] = off;
+        off += records_per_glyph(N_host[g], layout);
+    }
+    if (bytes) *bytes = off * shm_record_bytes(dtype, layout);
+    return SHM_OK;
+}
+
+shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph, const int64_t* seg,
+                     float* R, float* grad, float* normal, float* chart, int32_t* fij, int32_t* dev_status,
+                     shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
+    QueryArgs a;
+    a.L = view(lut);
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = glyph;
+    a.seg = glyph ? nullptr : seg;
+    a.R = R;
+    a.grad = grad;
+    a.normal = normal;
+    a.chart = chart;
+    a.fij = fij;
+    a.dev_status = dev_status;
+    return map_cuda(launch_query_fwd(a, (cudaStream_t)stream));
+}
+
+int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
+{
+    if (N < 1 || L < 0 || L > 20) return -1;
+    return (int64_t)(L + 1) * (L + 1) * 6 * (N + 2) * (N + 2) * 4 * (int64_t)sizeof(float);
+}
+
+shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream)
+{
+    if (N < 1 || N > (1 << 14) || L < 0 || L > 20 || !basis) return SHM_ERR_INVALID_ARG;
+    return map_cuda(launch_sh_basis(N, L, basis, (cudaStream_t)stream));
+}
+
+shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, size_t ws_bytes, shm_stream stream)
+{
+    (void)ws;
+    (void)ws_bytes;
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (!src) return SHM_ERR_INVALID_ARG;
+    const LutView v = view(lut);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (src->kind) {
+    case SHM_SRC_SH:
+        if (lut->N_uniform <= 0) return SHM_ERR_UNSUPPORTED;
+        if (src->L < 0 || src->L > 20 || !src->coeffs || !src->basis) return SHM_ERR_INVALID_ARG;
+        return map_cuda(launch_sh_build(v, lut->data, src->L, src->coeffs, src->basis, s));
+    case SHM_SRC_SAMPLES:
+    case SHM_SRC_BUMPS:
+    case SHM_SRC_FBM: {
+        if (src->kind == SHM_SRC_SAMPLES && (!src->samples || !src->sample_offset)) return SHM_ERR_INVALID_ARG;
+        if (src->kind == SHM_SRC_BUMPS && (!src->bump_offset || !src->mu || !src->amp || !src->width))
+            return SHM_ERR_INVALID_ARG;
+        if (src->kind == SHM_SRC_FBM && (src->octaves < 0 || src->octaves > 32 || (src->octaves > 0 && !src->keys)))
+            return SHM_ERR_INVALID_ARG;
+        const int mx = max_N_of(lut, s, &st);
+        if (st != SHM_OK) return st;
+        return map_cuda(launch_fd_build(v, lut->data, *src, mx, s));
+    }
+    default:
+        return SHM_ERR_INVALID_ARG;
+    }
+}
+
+shm_status shm_pack_lut(const shm_lut* src, const shm_lut* dst, shm_stream stream)
+{
+    shm_status st = check_lut(src);
+    if (st != SHM_OK) return st;
+    st = check_lut(dst);
+    if (st != SHM_OK) return st;
+    if (src->n_glyphs != dst->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if ((src->N_uniform > 0) != (dst->N_uniform > 0)) return SHM_ERR_INVALID_ARG;
+    if (src->N_uniform > 0 && src->N_uniform != dst->N_uniform) return SHM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mx = max_N_of(dst, s, &st);
+    if (st != SHM_OK) return st;
+    return map_cuda(launch_pack(view(src), view(dst), dst->data, mx, s));
+}
+
+shm_status shm_lut_bounds(const shm_lut* lut, float* rmax, shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (!rmax) return SHM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mx = max_N_of(lut, s, &st);
+    if (st != SHM_OK) return st;
+    return map_cuda(launch_bounds(view(lut), rmax, mx, s));
+}
+
+shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
+                              const int64_t* seg, const float* gR, const float* ggrad, const float* gnormal,
+                              const shm_lut* dlut, float* ddirs, int32_t* dev_status, shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    st = check_lut(dlut);
+    if (st != SHM_OK) return st;
+    if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
+    if (dlut->n_glyphs != lut->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if (Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
+    BackwardArgs a;
+    a.L = view(lut);
+    a.D = view(dlut);
+    a.dlut = (float*)dlut->data;
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = glyph;
+    a.seg = glyph ? nullptr : seg;
+    a.gR = gR;
+    a.ggrad = ggrad;
+    a.gnormal = gnormal;
+    a.ddirs = ddirs;
+    a.dev_status = dev_status;
+    return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
+}
+
+shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis, float* dcoeffs,
+                                  shm_stream stream)
+{
+    shm_status st = check_lut(dlut);
+    if (st != SHM_OK) return st;
+    if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL || dlut->N_uniform <= 0)
+        return SHM_ERR_UNSUPPORTED;
+    if (L < 0 || L > 20 || !basis || !dcoeffs) return SHM_ERR_INVALID_ARG;
+    return map_cuda(launch_sh_build_bwd(dlut->N_uniform, dlut->n_glyphs, L, (const float*)dlut->data, basis, dcoeffs,
+                                        (cudaStream_t)stream));
+}
+
+shm_status shm_sh_eval(int32_t L, int32_t n_glyphs, const float* coeffs, int64_t Q, const float* dirs,
+                       const int32_t* glyph, const int64_t* seg, float* R, float* grad, float* normal,
+                       int32_t* dev_status, shm_stream stream)
+{
+    if (L < 0 || L > 20 || n_glyphs <= 0 || !coeffs || Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
+    return map_cuda(launch_sh_eval(L, n_glyphs, coeffs, Q, dirs, glyph, glyph ? nullptr : seg, R, grad, normal,
+                                   dev_status, (cudaStream_t)stream));
+}
+
+int64_t shm_raycast_workspace_bytes(int32_t n_obj, int32_t W, int32_t H)
+{
+    if (n_obj < 0 || W <= 0 || H <= 0) return -1;
+    return raycast_workspace_bytes(n_obj, W, H);
+}
+
+shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj, const shm_camera* cam,
+                       const shm_raycast_params* prm, float* rgba, float* depth, float* normal, int32_t* obj_id,
+                       void* ws, size_t ws_bytes, int32_t* dev_status, shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (!cam || !prm || n_obj < 0 || (n_obj > 0 && !objs)) return SHM_ERR_INVALID_ARG;
+    if (cam->W <= 0 || cam->H <= 0 || cam->W > 65536 || cam->H > 65536) return SHM_ERR_INVALID_ARG;
+    if (prm->march < 1 || prm->march > 4096 || prm->bisect < 0 || prm->bisect > 64 || prm->newton < 0 ||
+        prm->newton > 64)
+        return SHM_ERR_INVALID_ARG;
+    const int64_t need = raycast_workspace_bytes(n_obj, cam->W, cam->H);
+    if (need > 0 && (!ws || (int64_t)ws_bytes < need)) return SHM_ERR_WORKSPACE;
+    return map_cuda(launch_raycast(view(lut), objs, n_obj, *cam, *prm, rgba, depth, normal, obj_id, ws, ws_bytes,
+                                   dev_status, (cudaStream_t)stream));
+}
+
+const char* shm_status_string(shm_status s)
+{
+    switch (s) {
+    case SHM_OK: return "ok";
+    case SHM_ERR_INVALID_ARG: return "invalid argument";
+    case SHM_ERR_UNSUPPORTED: return "unsupported dtype/layout/source combination";
+    case SHM_ERR_WORKSPACE: return "workspace missing or too small";
+    case SHM_ERR_CUDA: return "CUDA launch or runtime error";
+    case SHM_ERR_TIMEOUT: return "bounded device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+int32_t shm_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,677 @@
+// Bake kernels (arXiv 2602.20063, Algorithm 1 and §3.3 "Derivative computation"):
+//
+//   k_sh_basis      per stored texel (gutter included) and SH function Y_k the record
+//                   (Y, Y_u h, Y_v h, Y_uv h^2): Y and its Cartesian gradient / Hessian from the
+//                   polynomial form of the real SH, carried to the face chart by the chain rule
+//                   r_u = grad Y . dw/du,  r_uv = (dw/du)^T H (dw/dv) + grad Y . d2w/dudv.
+//   k_sh_gemm       lut[g][t][ch] = sum_k c[g][k] basis[k][t][ch] - r0[g] (ch 0): the bake of many
+//                   glyphs as one [G x K] x [K x 4T] contraction (SIMT float32 reference engine).
+//   k_sh_gemm_bwd   dc[g][k] = sum_{t,ch} dlut[g][t][ch] basis[k][t][ch].
+//   k_fd_build      central differences on a sample grid with a one-texel bake margin, from
+//                   stored samples, Gaussian bumps or value-noise fBm evaluated in the kernel.
+//   k_pack          re-encode a table into another dtype / layout.
+//   k_bounds        per-glyph bound of |interpolated r| for ray bracketing (§3.1).
+//   k_sh_eval       direct SH value, S^2 gradient and normal (ground truth, no table).
+//
+// SH convention: orthonormal real SH, index l*l + l + m, no Condon-Shortley phase,
+// Y_l0 = P~_l^0(z), Y_lm = sqrt2 P~_l^m(z) Re (x+iy)^m, Y_l-m = sqrt2 P~_l^m(z) Im (x+iy)^m, where
+// P~_l^m = K_lm d^m P_l/dz^m comes from the normalised recurrences
+//   P~_0^0 = 1/sqrt(4 pi),  P~_m^m = sqrt((2m+1)/(2m)) P~_{m-1}^{m-1},  P~_{m+1}^m = sqrt(2m+3) z P~_m^m,
+//   P~_l^m = a_lm (z P~_{l-1}^m - b_lm P~_{l-2}^m),  a_lm = sqrt((4l^2-1)/(l^2-m^2)),
+//   b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)),
+// and K_lm d^{m+1}P_l/dz^{m+1} = sqrt((l-m)(l+m+1)) P~_l^{m+1} (no overflow for any L).
+#include "shm_internal.h"
+
+namespace shm {
+
+constexpr int SH_LMAX = 20;
+
+// ------------------------------------------------------------------------------------------
+// Normalised associated Legendre table T[l(l+1)/2 + m], 0 <= m <= l <= L, in Qbar form.
+__device__ __forceinline__ void legendre_table(int L, float z, float* T)
+{
+    T[0] = 0.28209479177387814f;  // 1/sqrt(4 pi)
+    for (int m = 0; m <= L; ++m) {
+        const int im = m * (m + 1) / 2 + m;
+        if (m > 0) {
+            const int ip = (m - 1) * m / 2 + (m - 1);
+            T[im] = T[ip] * sqrtf((2.0f * m + 1.0f) / (2.0f * m));
+        }
+        if (m + 1 <= L) T[(m + 1) * (m + 2) / 2 + m] = sqrtf(2.0f * m + 3.0f) * z * T[im];
+        for (int l = m + 2; l <= L; ++l) {
+            const float l2 = (float)(l * l), m2 = (float)(m * m), lm1 = (float)((l - 1) * (l - 1));
+            const float a = sqrtf((4.0f * l2 - 1.0f) / (l2 - m2));
+            const float b = sqrtf((lm1 - m2) / (4.0f * lm1 - 1.0f));
+            T[l * (l + 1) / 2 + m] = a * (z * T[(l - 1) * l / 2 + m] - b * T[(l - 2) * (l - 1) / 2 + m]);
+        }
+    }
+}
+
+__device__ __forceinline__ float tab(const float* T, int l, int m)
+{
+    return (m <= l) ? T[l * (l + 1) / 2 + m] : 0.0f;
+}
+
+// Value, Cartesian gradient and Hessian (xx, xy, yy, xz, yz, zz) of Y_lm at the unit vector w.
+struct YDer {
+    float v, gx, gy, gz, hxx, hxy, hyy, hxz, hyz, hzz;
+};
+
+// A = C_m (cosine part) or S_m (sine part) of (x + iy)^m, with derivatives from
+// d/dx (x+iy)^m = m (x+iy)^{m-1},  d/dy (x+iy)^m = i m (x+iy)^{m-1}.
+__device__ __forceinline__ YDer ylm_derivs(const float* T, int l, int m, bool sine, const float* C, const float* S)
+{
+    YDer y;
+    const float q0 = tab(T, l, m);
+    const float f1 = sqrtf((float)((l - m) * (l + m + 1)));
+    const float q1 = f1 * tab(T, l, m + 1);
+    const float q2 = f1 * sqrtf((float)max(0, (l - m - 1) * (l + m + 2))) * tab(T, l, m + 2);
+    float A, Ax, Ay, Axx, Axy, Ayy;
+    if (m == 0) {
+        A = 1.0f; Ax = Ay = Axx = Axy = Ayy = 0.0f;
+    } else if (!sine) {
+        A = C[m];
+        Ax = m * C[m - 1];
+        Ay = -m * S[m - 1];
+        const float mm = (float)(m * (m - 1));
+        Axx = m >= 2 ? mm * C[m - 2] : 0.0f;
+        Axy = m >= 2 ? -mm * S[m - 2] : 0.0f;
+        Ayy = -Axx;
+    } else {
+        A = S[m];
+        Ax = m * S[m - 1];
+        Ay = m * C[m - 1];
+        const float mm = (float)(m * (m - 1));
+        Axx = m >= 2 ? mm * S[m - 2] : 0.0f;
+        Axy = m >= 2 ? mm * C[m - 2] : 0.0f;
+        Ayy = -Axx;
+    }
+    const float sc = (m == 0) ? 1.0f : 1.41421356237309515f;
+    y.v = sc * q0 * A;
+    y.gx = sc * q0 * Ax;
+    y.gy = sc * q0 * Ay;
+    y.gz = sc * q1 * A;
+    y.hxx = sc * q0 * Axx;
+    y.hxy = sc * q0 * Axy;
+    y.hyy = sc * q0 * Ayy;
+    y.hxz = sc * q1 * Ax;
+    y.hyz = sc * q1 * Ay;
+    y.hzz = sc * q2 * A;
+    return y;
+}
+
+__device__ __forceinline__ void cs_table(int L, float x, float y, float* C, float* S)
+{
+    C[0] = 1.0f;
+    S[0] = 0.0f;
+    for (int m = 1; m <= L; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+}
+
+// Unit vector of chart axis `axis` (0..2) with sign.
+__device__ __forceinline__ Vec3 axis_vec(int axis, float sgn)
+{
+    return Vec3{axis == 0 ? sgn : 0.0f, axis == 1 ? sgn : 0.0f, axis == 2 ? sgn : 0.0f};
+}
+
+__device__ __forceinline__ float dot3(const Vec3& a, const Vec3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Direction of texel-centre chart coordinates (X, Y) = (2u-1, 2v-1) on face f, with the
+// tangents e1 = dw/du, e2 = dw/dv and the mixed second derivative W = d2w/dudv.
+struct TexelFrame {
+    Vec3 w, e1, e2, W;
+};
+
+__device__ __forceinline__ TexelFrame texel_frame(int f, float X, float Y)
+{
+    const int k = f >> 1;
+    const float sg = (f & 1) ? -1.0f : 1.0f;
+    const Vec3 a = axis_vec(k, sg), b = axis_vec((k + 1) % 3, 1.0f), c = axis_vec((k + 2) % 3, 1.0f);
+    const Vec3 wt{a.x + X * b.x + Y * c.x, a.y + X * b.y + Y * c.y, a.z + X * b.z + Y * c.z};
+    const float rho2 = 1.0f + X * X + Y * Y;
+    const float rho = sqrtf(rho2);
+    const float ir = 1.0f / rho;
+    TexelFrame T;
+    T.w = Vec3{wt.x * ir, wt.y * ir, wt.z * ir};
+    // e1 = (2/rho)(b - w (w.b)), w.b = X/rho; e2 likewise with c, Y
+    const float wb = X * ir, wc = Y * ir;
+    T.e1 = Vec3{2.0f * ir * (b.x - T.w.x * wb), 2.0f * ir * (b.y - T.w.y * wb), 2.0f * ir * (b.z - T.w.z * wb)};
+    T.e2 = Vec3{2.0f * ir * (c.x - T.w.x * wc), 2.0f * ir * (c.y - T.w.y * wc), 2.0f * ir * (c.z - T.w.z * wc)};
+    // W = (4/rho^3)(-Y b - X c) + (12 X Y / rho^5) w~
+    const float i3 = 4.0f * ir * ir * ir, i5 = 12.0f * X * Y * ir * ir * ir * ir * ir;
+    T.W = Vec3{i3 * (-Y * b.x - X * c.x) + i5 * wt.x, i3 * (-Y * b.y - X * c.y) + i5 * wt.y,
+               i3 * (-Y * b.z - X * c.z) + i5 * wt.z};
+    return T;
+}
+
+__global__ void __launch_bounds__(128) k_sh_basis(int N, int L, float* __restrict__ basis)
+{
+    const int P = N + 2;
+    const int T = 6 * P * P;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int f = t / (P * P), rem = t % (P * P), j = rem / P, i = rem % P;
+    // texel centre u_i = (i - 1/2)/N -> 2u - 1 = (2i - 1 - N)/N
+    const float X = (float)(2 * i - 1 - N) / (float)N;
+    const float Y = (float)(2 * j - 1 - N) / (float)N;
+    const TexelFrame F = texel_frame(f, X, Y);
+    float Tl[(SH_LMAX + 1) * (SH_LMAX + 2) / 2];
+    float C[SH_LMAX + 1], S[SH_LMAX + 1];
+    legendre_table(L, F.w.z, Tl);
+    cs_table(L, F.w.x, F.w.y, C, S);
+    const float h = 1.0f / (float)N;
+    for (int l = 0; l <= L; ++l) {
+        for (int mm = -l; mm <= l; ++mm) {
+            const int m = mm < 0 ? -mm : mm;
+            const YDer y = ylm_derivs(Tl, l, m, mm < 0, C, S);
+            const float ru = y.gx * F.e1.x + y.gy * F.e1.y + y.gz * F.e1.z;
+            const float rv = y.gx * F.e2.x + y.gy * F.e2.y + y.gz * F.e2.z;
+            const float e1He2 = y.hxx * F.e1.x * F.e2.x + y.hyy * F.e1.y * F.e2.y + y.hzz * F.e1.z * F.e2.z +
+                                y.hxy * (F.e1.x * F.e2.y + F.e1.y * F.e2.x) +
+                                y.hxz * (F.e1.x * F.e2.z + F.e1.z * F.e2.x) +
+                                y.hyz * (F.e1.y * F.e2.z + F.e1.z * F.e2.y);
+            const float ruv = e1He2 + y.gx * F.W.x + y.gy * F.W.y + y.gz * F.W.z;
+            const int k = l * l + l + mm;
+            reinterpret_cast<float4*>(basis)[(int64_t)k * T + t] = make_float4(y.v, ru * h, rv * h, ruv * h * h);
+        }
+    }
+}
+
+cudaError_t launch_sh_basis(int N, int L, float* basis, cudaStream_t s)
+{
+    const int T = 6 * (N + 2) * (N + 2);
+    k_sh_basis<<<(T + 127) / 128, 128, 0, s>>>(N, L, basis);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Generic record store / load for any dtype and layout.
+__device__ __forceinline__ uint2 f4_to_h4(float4 v)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+__device__ __forceinline__ uint2 f4_to_b4(float4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+__device__ __forceinline__ void store_rec(void* data, int dtype, int64_t rec, float4 v)
+{
+    if (dtype == SHM_F32) reinterpret_cast<float4*>(data)[rec] = v;
+    else if (dtype == SHM_F16) reinterpret_cast<uint2*>(data)[rec] = f4_to_h4(v);
+    else reinterpret_cast<uint2*>(data)[rec] = f4_to_b4(v);
+}
+
+__device__ __forceinline__ float4 load_rec_any(const void* data, int dtype, int64_t rec)
+{
+    if (dtype == SHM_F32) return load_rec<SHM_F32>(data, rec);
+    if (dtype == SHM_F16) return load_rec<SHM_F16>(data, rec);
+    return load_rec<SHM_BF16>(data, rec);
+}
+
+// Store texel (i, j) of face f: one record (texel layout) or up to four cell corners.
+__device__ __forceinline__ void store_texel(void* data, int dtype, int layout, const GlyphRef& G, int f, int j,
+                                            int i, float4 v)
+{
+    if (layout == SHM_LAYOUT_TEXEL) {
+        const int64_t P = G.N + 2;
+        store_rec(data, dtype, G.base + ((int64_t)f * P + j) * P + i, v);
+    } else {
+        const int64_t P = G.N + 1;
+        for (int cj = j - 1; cj <= j; ++cj) {
+            if (cj < 0 || cj > G.N) continue;
+            for (int ci = i - 1; ci <= i; ++ci) {
+                if (ci < 0 || ci > G.N) continue;
+                const int corner = (j - cj) * 2 + (i - ci);
+                store_rec(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + corner, v);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float4 load_texel(const void* data, int dtype, int layout, const GlyphRef& G, int f,
+                                             int j, int i)
+{
+    if (layout == SHM_LAYOUT_TEXEL) {
+        const int64_t P = G.N + 2;
+        return load_rec_any(data, dtype, G.base + ((int64_t)f * P + j) * P + i);
+    }
+    const int64_t P = G.N + 1;
+    const int ci = min(i, G.N), cj = min(j, G.N);
+    return load_rec_any(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + (j - cj) * 2 + (i - ci));
+}
+
+// ------------------------------------------------------------------------------------------
+// SIMT bake contraction: tile of 32 glyphs x 64 texels (x 4 channels), K in chunks of 16.
+constexpr int GT_G = 32, GT_T = 64, GT_K = 16;
+
+__global__ void __launch_bounds__(256) k_sh_gemm(LutView out, void* data, int K, const float* __restrict__ coeffs,
+                                                 const float* __restrict__ basis)
+{
+    __shared__ __align__(16) float Cs[GT_K][GT_G];
+    __shared__ __align__(16) float4 Bs[GT_K][GT_T];
+    const int N = out.N_uniform;
+    const int T = 6 * (N + 2) * (N + 2);
+    const int G = out.n_glyphs;
+    const int g0 = blockIdx.y * GT_G, t0 = blockIdx.x * GT_T;
+    const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
+    float4 acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4* B4 = reinterpret_cast<const float4*>(basis);
+    for (int k0 = 0; k0 < K; k0 += GT_K) {
+        for (int e = tid; e < GT_K * GT_G; e += 256) {
+            const int kk = e % GT_K, gg = e / GT_K;
+            const int g = g0 + gg, k = k0 + kk;
+            Cs[kk][gg] = (g < G && k < K) ? __ldg(coeffs + (int64_t)g * K + k) : 0.0f;
+        }
+        for (int e = tid; e < GT_K * GT_T; e += 256) {
+            const int kk = e / GT_T, tt = e % GT_T;
+            const int k = k0 + kk, t = t0 + tt;
+            Bs[kk][tt] = (k < K && t < T) ? __ldg(B4 + (int64_t)k * T + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GT_K; ++kk) {
+            const float4 b = Bs[kk][tx];
+            const float4 ca = *reinterpret_cast<const float4*>(&Cs[kk][ty * 8]);
+            const float4 cb = *reinterpret_cast<const float4*>(&Cs[kk][ty * 8 + 4]);
+            const float cv[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                acc[r].x = fmaf(cv[r], b.x, acc[r].x);
+                acc[r].y = fmaf(cv[r], b.y, acc[r].y);
+                acc[r].z = fmaf(cv[r], b.z, acc[r].z);
+                acc[r].w = fmaf(cv[r], b.w, acc[r].w);
+            }
+        }
+        __syncthreads();
+    }
+    const int t = t0 + tx;
+    if (t >= T) return;
+    const int P = N + 2;
+    const int f = t / (P * P), rem = t % (P * P), j = rem / P, i = rem % P;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int g = g0 + ty * 8 + r;
+        if (g >= G) break;
+        const GlyphRef Gr = glyph_ref(out, g);
+        float4 v = acc[r];
+        v.x -= Gr.r0;
+        store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
+    }
+}
+
+cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* coeffs, const float* basis,
+                            cudaStream_t s)
+{
+    const int N = out.N_uniform;
+    const int T = 6 * (N + 2) * (N + 2);
+    const int K = (L + 1) * (L + 1);
+    dim3 grid((T + GT_T - 1) / GT_T, (out.n_glyphs + GT_G - 1) / GT_G);
+    k_sh_gemm<<<grid, 256, 0, s>>>(out, data, K, coeffs, basis);
+    return cudaGetLastError();
+}
+
+// dc[g][k] = sum_r dlut[g][r] basis[k][r], r over 4T scalars.  Tile 64 glyphs x 32 k, the
+// reduction split over blockIdx.z and combined with atomics into a zeroed dcoeffs.
+constexpr int BG = 64, BK = 32, BR = 32;
+
+__global__ void __launch_bounds__(256) k_sh_gemm_bwd(int R4, int G, int K, const float* __restrict__ dlut,
+                                                     const float* __restrict__ basis, float* __restrict__ dc,
+                                                     int r_per_split)
+{
+    __shared__ __align__(16) float Ds[BR][BG];
+    __shared__ __align__(16) float Bs[BR][BK];
+    const int g0 = blockIdx.x * BG, k0 = blockIdx.y * BK;
+    const int rb = blockIdx.z * r_per_split, re = min(R4, rb + r_per_split);
+    const int tid = threadIdx.x, tg = tid & 15, tk = tid >> 4;  // 4 glyphs x 2 k per thread
+    float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int r0 = rb; r0 < re; r0 += BR) {
+        for (int e = tid; e < BR * BG; e += 256) {
+            const int rr = e % BR, gg = e / BR;
+            const int g = g0 + gg, r = r0 + rr;
+            Ds[rr][gg] = (g < G && r < re) ? __ldg(dlut + (int64_t)g * R4 + r) : 0.0f;
+        }
+        for (int e = tid; e < BR * BK; e += 256) {
+            const int rr = e % BR, kk = e / BR;
+            const int k = k0 + kk, r = r0 + rr;
+            Bs[rr][kk] = (k < K && r < re) ? __ldg(basis + (int64_t)k * R4 + r) : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int rr = 0; rr < BR; ++rr) {
+            const float4 d = *reinterpret_cast<const float4*>(&Ds[rr][tg * 4]);
+            const float2 b = *reinterpret_cast<const float2*>(&Bs[rr][tk * 2]);
+            const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                acc[a][0] = fmaf(dv[a], b.x, acc[a][0]);
+                acc[a][1] = fmaf(dv[a], b.y, acc[a][1]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 2; ++c) {
+            const int g = g0 + tg * 4 + a, k = k0 + tk * 2 + c;
+            if (g < G && k < K) atomicAdd(dc + (int64_t)g * K + k, acc[a][c]);
+        }
+}
+
+cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
+                                cudaStream_t s)
+{
+    const int K = (L + 1) * (L + 1);
+    const int R4 = 4 * 6 * (N + 2) * (N + 2);
+    cudaError_t e = cudaMemsetAsync(dcoeffs, 0, sizeof(float) * (size_t)G * K, s);
+    if (e != cudaSuccess) return e;
+    const int gx = (G + BG - 1) / BG, ky = (K + BK - 1) / BK;
+    int splits = (sm_count() * 4 + gx * ky - 1) / (gx * ky);
+    const int max_splits = (R4 + BR - 1) / BR;
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    int per = (R4 + splits - 1) / splits;
+    per = (per + BR - 1) / BR * BR;
+    splits = (R4 + per - 1) / per;
+    k_sh_gemm_bwd<<<dim3(gx, ky, splits), 256, 0, s>>>(R4, G, K, dlut, basis, dcoeffs, per);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Procedural sources (radial depth-map impostors §4.9, procedural planets §4.10).
+__device__ __forceinline__ void pcg3d(uint32_t& x, uint32_t& y, uint32_t& z)
+{
+    x = x * 1664525u + 1013904223u;
+    y = y * 1664525u + 1013904223u;
+    z = z * 1664525u + 1013904223u;
+    x += y * z;
+    y += z * x;
+    z += x * y;
+    x ^= x >> 16;
+    y ^= y >> 16;
+    z ^= z >> 16;
+    x += y * z;
+    y += z * x;
+    z += x * y;
+}
+
+__device__ __forceinline__ float lattice_value(int ix, int iy, int iz, uint32_t k0, uint32_t k1, uint32_t k2)
+{
+    uint32_t x = (uint32_t)ix + k0, y = (uint32_t)iy + k1, z = (uint32_t)iz + k2;
+    pcg3d(x, y, z);
+    return (float)(x >> 8) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+__device__ __forceinline__ float quintic(float t) { return t * t * t * (t * (t * 6.0f - 15.0f) + 10.0f); }
+
+__device__ float value_noise(float px, float py, float pz, uint32_t k0, uint32_t k1, uint32_t k2)
+{
+    const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    const float wx = quintic(px - fx), wy = quintic(py - fy), wz = quintic(pz - fz);
+    float c[2][2];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy) {
+            const float v0 = lattice_value(ix, iy + dy, iz + dz, k0, k1, k2);
+            const float v1 = lattice_value(ix + 1, iy + dy, iz + dz, k0, k1, k2);
+            c[dz][dy] = v0 + wx * (v1 - v0);
+        }
+    const float e0 = c[0][0] + wy * (c[0][1] - c[0][0]);
+    const float e1 = c[1][0] + wy * (c[1][1] - c[1][0]);
+    return e0 + wz * (e1 - e0);
+}
+
+__device__ float fbm(const Vec3& w, const shm_source& src)
+{
+    float sum = 0.0f, freq = src.base_freq, amp = 1.0f;
+    for (int o = 0; o < src.octaves; ++o) {
+        const uint32_t* key = src.keys + 3 * o;
+        sum += amp * value_noise(w.x * freq, w.y * freq, w.z * freq, __ldg(key), __ldg(key + 1), __ldg(key + 2));
+        freq *= src.lacunarity;
+        amp *= src.gain;
+    }
+    return src.amplitude * sum;
+}
+
+// ------------------------------------------------------------------------------------------
+// FD bake: 16x16 texel tile per CTA, 18x18 samples (one-texel halo) in shared memory.
+constexpr int FT = 16, FS = FT + 2, MAX_BUMPS_SMEM = 128;
+
+__global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_source src, int g_base)
+{
+    __shared__ float Sm[FS][FS];
+    __shared__ float bump[MAX_BUMPS_SMEM][5];
+    const int g = g_base + blockIdx.z, f = blockIdx.y;
+    const GlyphRef Gr = glyph_ref(out, g);
+    const int N = Gr.N, P = N + 2, S = N + 4;
+    const int tiles = (P + FT - 1) / FT;
+    if ((int)blockIdx.x >= tiles * tiles) return;
+    const int i0 = (blockIdx.x % tiles) * FT, j0 = (blockIdx.x / tiles) * FT;
+    const int tid = threadIdx.x;
+    const int k = f >> 1;
+    const float sg = (f & 1) ? -1.0f : 1.0f;
+    const Vec3 a = axis_vec(k, sg), bb = axis_vec((k + 1) % 3, 1.0f), cc = axis_vec((k + 2) % 3, 1.0f);
+
+    // Two sample slots per thread (18 x 18 = 324 samples, 256 threads).  Sample-grid index
+    // (ii, jj) holds texel (ii-1, jj-1) at u = (ii - 3/2)/N, i.e. 2u - 1 = (2 ii - 3 - N)/N.
+    float acc[2] = {0.f, 0.f};
+    Vec3 w[2];
+    bool live[2];
+    for (int r = 0; r < 2; ++r) {
+        const int e = tid + r * 256;
+        const int ii = i0 + (e % FS), jj = j0 + (e / FS);
+        live[r] = (e < FS * FS) && ii < S && jj < S;
+        const float X = (float)(2 * ii - 3 - N) / (float)N;
+        const float Y = (float)(2 * jj - 3 - N) / (float)N;
+        const float ir = rsqrtf(1.0f + X * X + Y * Y);
+        w[r] = Vec3{(a.x + X * bb.x + Y * cc.x) * ir, (a.y + X * bb.y + Y * cc.y) * ir,
+                    (a.z + X * bb.z + Y * cc.z) * ir};
+        if (!live[r]) continue;
+        if (src.kind == SHM_SRC_SAMPLES)
+            acc[r] = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
+        else if (src.kind == SHM_SRC_FBM)
+            acc[r] = fbm(w[r], src);
+    }
+    // Bumps: the sum without the leading 1 is kept in the samples (stored = sum + 1 - r0).
+    float base = 0.0f;
+    if (src.kind == SHM_SRC_BUMPS) {
+        base = 1.0f - Gr.r0;
+        const int64_t b_lo = __ldg(src.bump_offset + g), b_hi = __ldg(src.bump_offset + g + 1);
+        for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
+            const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
+            __syncthreads();
+            for (int e = tid; e < nb; e += 256) {
+                bump[e][0] = __ldg(src.mu + 3 * (bc + e));
+                bump[e][1] = __ldg(src.mu + 3 * (bc + e) + 1);
+                bump[e][2] = __ldg(src.mu + 3 * (bc + e) + 2);
+                bump[e][3] = __ldg(src.amp + bc + e);
+                const float wd = __ldg(src.width + bc + e);
+                bump[e][4] = -0.5f / (wd * wd);
+            }
+            __syncthreads();
+            for (int r = 0; r < 2; ++r) {
+                if (!live[r]) continue;
+                float sum = acc[r];
+                for (int q = 0; q < nb; ++q) {
+                    const float dx = w[r].x - bump[q][0], dy = w[r].y - bump[q][1], dz = w[r].z - bump[q][2];
+                    sum = fmaf(bump[q][3], expf((dx * dx + dy * dy + dz * dz) * bump[q][4]), sum);
+                }
+                acc[r] = sum;
+            }
+        }
+    }
+    for (int r = 0; r < 2; ++r) {
+        const int e = tid + r * 256;
+        if (e < FS * FS) Sm[e / FS][e % FS] = acc[r];
+    }
+    __syncthreads();
+    const int ti = tid % FT, tj = tid / FT;
+    const int i = i0 + ti, j = j0 + tj;
+    if (i >= P || j >= P) return;
+    const int si = ti + 1, sj = tj + 1;  // texel (i, j) is sample (i+1, j+1): tile-local (ti+1, tj+1)
+    float4 v;
+    v.x = Sm[sj][si] + base;
+    v.y = 0.5f * (Sm[sj][si + 1] - Sm[sj][si - 1]);
+    v.z = 0.5f * (Sm[sj + 1][si] - Sm[sj - 1][si]);
+    v.w = 0.25f * ((Sm[sj + 1][si + 1] - Sm[sj - 1][si + 1]) - (Sm[sj + 1][si - 1] - Sm[sj - 1][si - 1]));
+    store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
+}
+
+cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, int max_N, cudaStream_t s)
+{
+    const int tiles = (max_N + 2 + FT - 1) / FT;
+    for (int g0 = 0; g0 < out.n_glyphs; g0 += 65535) {
+        const int n = min(65535, out.n_glyphs - g0);
+        k_fd_build<<<dim3(tiles * tiles, 6, n), 256, 0, s>>>(out, data, src, g0);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Pack: one thread per destination record.
+__global__ void __launch_bounds__(256) k_pack(LutView src, LutView dst, void* ddata, int g_base)
+{
+    const int g = g_base + blockIdx.y;
+    const GlyphRef Gs = glyph_ref(src, g), Gd = glyph_ref(dst, g);
+    const int N = Gd.N;
+    const int64_t nrec = records_per_glyph(N, dst.layout);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += (int64_t)gridDim.x * blockDim.x) {
+        const float dr0 = Gs.r0 - Gd.r0;
+        if (dst.layout == SHM_LAYOUT_TEXEL) {
+            const int P = N + 2;
+            const int f = (int)(r / ((int64_t)P * P)), rem = (int)(r % ((int64_t)P * P)), j = rem / P, i = rem % P;
+            float4 v = load_texel(src.data, src.dtype, src.layout, Gs, f, j, i);
+            v.x += dr0;
+            store_rec(ddata, dst.dtype, Gd.base + r, v);
+        } else {
+            const int P = N + 1;
+            const int f = (int)(r / ((int64_t)P * P)), rem = (int)(r % ((int64_t)P * P)), j = rem / P, i = rem % P;
+            for (int corner = 0; corner < 4; ++corner) {
+                float4 v = load_texel(src.data, src.dtype, src.layout, Gs, f, j + (corner >> 1), i + (corner & 1));
+                v.x += dr0;
+                store_rec(ddata, dst.dtype, (Gd.base + r) * 4 + corner, v);
+            }
+        }
+    }
+}
+
+cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, int max_N, cudaStream_t s)
+{
+    const int64_t maxrec = records_per_glyph(max_N, dst.layout);
+    int64_t bx = (maxrec + 255) / 256;
+    if (bx > 65535) bx = 65535;
+    for (int g0 = 0; g0 < dst.n_glyphs; g0 += 65535)
+        k_pack<<<dim3((unsigned)bx, min(65535, dst.n_glyphs - g0)), 256, 0, s>>>(src, dst, dst_data, g0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Bounds: per cell, |r| <= max|r0 + r_ab| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16 over the
+// cell's four corners (value weights are >= 0 and sum to 1; sum_a |H^d_a| = s(1-s) <= 1/4).
+__global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, int g_base)
+{
+    const int g = g_base + blockIdx.y;
+    const GlyphRef G = glyph_ref(L, g);
+    const int N = G.N, P = N + 1;
+    const int64_t ncell = 6LL * P * P;
+    float best = 0.0f;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(c / ((int64_t)P * P)), rem = (int)(c % ((int64_t)P * P)), j = rem / P, i = rem % P;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+        for (int corner = 0; corner < 4; ++corner) {
+            const float4 v = load_texel(L.data, L.dtype, L.layout, G, f, j + (corner >> 1), i + (corner & 1));
+            m0 = fmaxf(m0, fabsf(G.r0 + v.x));
+            m1 = fmaxf(m1, fabsf(v.y));
+            m2 = fmaxf(m2, fabsf(v.z));
+            m3 = fmaxf(m3, fabsf(v.w));
+        }
+        best = fmaxf(best, m0 + 0.25f * (m1 + m2) + 0.0625f * m3);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(rmax + g), __float_as_int(best));
+}
+
+cudaError_t launch_bounds(const LutView& L, float* rmax, int max_N, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(float) * (size_t)L.n_glyphs, s);
+    if (e != cudaSuccess) return e;
+    const int64_t ncell = 6LL * (max_N + 1) * (max_N + 1);
+    int64_t bx = (ncell + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    for (int g0 = 0; g0 < L.n_glyphs; g0 += 65535)
+        k_bounds<<<dim3((unsigned)bx, min(65535, L.n_glyphs - g0)), 256, 0, s>>>(L, rmax, g0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Direct SH: r = sum_k c_k Y_k(w), Euclidean gradient of the polynomial projected onto the tangent
+// plane gives grad_{S^2} r, then the §3.4 normal.
+__global__ void __launch_bounds__(128) k_sh_eval(int L, int G, const float* __restrict__ coeffs, int64_t Q,
+                                                 const float* __restrict__ dirs, const int32_t* __restrict__ glyph,
+                                                 const int64_t* __restrict__ seg, float* R, float* grad,
+                                                 float* normal, int32_t* dev_status)
+{
+    const int K = (L + 1) * (L + 1);
+    uint32_t status = 0;
+    const float qnan = __int_as_float(0x7fc00000);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+        int g = 0;
+        if (glyph) g = __ldg(glyph + q);
+        else if (seg) g = (q < __ldg(seg)) ? -1 : seg_find(seg, G, q);
+        const float d0 = __ldg(dirs + 3 * q), d1 = __ldg(dirs + 3 * q + 1), d2 = __ldg(dirs + 3 * q + 2);
+        const float n2 = d0 * d0 + d1 * d1 + d2 * d2;
+        bool ok = (g >= 0 && g < G);
+        if (!ok) status |= SHM_DEV_BOUNDS;
+        if (ok && !(n2 > 0.0f && n2 <= 3.0e38f)) { ok = false; status |= SHM_DEV_NONFINITE; }
+        float r = qnan;
+        Vec3 gs{qnan, qnan, qnan}, nn{qnan, qnan, qnan};
+        if (ok) {
+            const float il = rsqrtf(n2);
+            const Vec3 w{d0 * il, d1 * il, d2 * il};
+            float Tl[(SH_LMAX + 1) * (SH_LMAX + 2) / 2];
+            float C[SH_LMAX + 1], S[SH_LMAX + 1];
+            legendre_table(L, w.z, Tl);
+            cs_table(L, w.x, w.y, C, S);
+            const float* c = coeffs + (int64_t)g * K;
+            float rv = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            for (int l = 0; l <= L; ++l)
+                for (int mm = -l; mm <= l; ++mm) {
+                    const int m = mm < 0 ? -mm : mm;
+                    const YDer y = ylm_derivs(Tl, l, m, mm < 0, C, S);
+                    const float ck = __ldg(c + l * l + l + mm);
+                    rv = fmaf(ck, y.v, rv);
+                    gx = fmaf(ck, y.gx, gx);
+                    gy = fmaf(ck, y.gy, gy);
+                    gz = fmaf(ck, y.gz, gz);
+                }
+            const float wg = w.x * gx + w.y * gy + w.z * gz;
+            r = rv;
+            gs = Vec3{gx - w.x * wg, gy - w.y * wg, gz - w.z * wg};
+            nn = surface_normal(d0, d1, d2, r, gs);
+        }
+        if (R) R[q] = r;
+        if (grad) { grad[3 * q] = gs.x; grad[3 * q + 1] = gs.y; grad[3 * q + 2] = gs.z; }
+        if (normal) { normal[3 * q] = nn.x; normal[3 * q + 1] = nn.y; normal[3 * q + 2] = nn.z; }
+    }
+    report_status(dev_status, status);
+}
+
+cudaError_t launch_sh_eval(int L, int G, const float* coeffs, int64_t Q, const float* dirs, const int32_t* glyph,
+                           const int64_t* seg, float* R, float* grad, float* normal, int32_t* dev_status,
+                           cudaStream_t s)
+{
+    if (Q == 0) return cudaSuccess;
+    int64_t blocks = (Q + 127) / 128;
+    const int64_t cap = (int64_t)sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+    k_sh_eval<<<(unsigned)blocks, 128, 0, s>>>(L, G, coeffs, Q, dirs, glyph, seg, R, grad, normal, dev_status);
+    return cudaGetLastError();
+}
+
+}  // namespace shm

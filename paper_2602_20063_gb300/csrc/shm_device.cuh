@@ -1,0 +1,283 @@
+// Device building blocks of the Spherical Hermite Map hot path (arXiv 2602.20063), sm_103a.
+//
+//   chart   §3.2: direction -> axis k, face f, chart coordinates, cell (i, j), local (s, t)
+//   fetch   §3.3: the 2x2 texel footprint of one cell, any record dtype / layout
+//   hermite §3.3: value and chart derivatives by tensor-product cubic Hermite interpolation
+//   grad    §3.4: S^2 gradient from chart derivatives, normal
+//
+// Everything is float32.  Two numerical choices differ from a literal transcription:
+//   * the cell coordinate x = uN + 1/2 is formed from a double-float quotient
+//     q = d_{k+1}/|d_k| (hi + lo) so that s, t carry ~1e-8 absolute error even at N = 2048,
+//     where a plain float x = uN + 1/2 would lose ~1e-4 of a cell;
+//   * the 1-D Hermite sums are evaluated in difference form H0 f0 + H1 f1 = f0 + H1 (f1 - f0),
+//     so the large common value of neighbouring texels cancels exactly before it is scaled
+//     by N in the chart derivative.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/shm.h"
+
+namespace shm {
+
+// ------------------------------------------------------------------------------------------
+// Table addressing
+struct LutView {
+    const void* data;
+    const int32_t* N;
+    const int64_t* offset;
+    const float* r0;
+    int32_t n_glyphs;
+    int32_t N_uniform;
+    int32_t dtype;
+    int32_t layout;
+};
+
+__host__ __device__ __forceinline__ int64_t records_per_glyph(int N, int layout)
+{
+    const int64_t P = (layout == SHM_LAYOUT_CELL) ? (int64_t)N + 1 : (int64_t)N + 2;
+    return 6 * P * P;
+}
+
+struct GlyphRef {
+    int N;
+    int64_t base;  // first record
+    float r0;
+};
+
+__device__ __forceinline__ GlyphRef glyph_ref(const LutView& L, int g)
+{
+    GlyphRef r;
+    if (L.N_uniform > 0) {
+        r.N = L.N_uniform;
+        r.base = (int64_t)g * records_per_glyph(L.N_uniform, L.layout);
+    } else {
+        r.N = __ldg(L.N + g);
+        r.base = __ldg(L.offset + g);
+    }
+    r.r0 = L.r0 ? __ldg(L.r0 + g) : 0.0f;
+    return r;
+}
+
+// ------------------------------------------------------------------------------------------
+// Chart (§3.2)
+struct Chart {
+    int k, k1, k2;   // dominant axis and the two chart axes
+    float sigma;     // sign of d_k
+    float m;         // |d_k|
+    float x, y;      // chart coordinates 2u-1 = d_k1/|d_k|, 2v-1 = d_k2/|d_k|
+    int f;           // face 2k + (d_k < 0)
+};
+
+__device__ __forceinline__ float pick3(int c, float a0, float a1, float a2)
+{
+    return c == 0 ? a0 : (c == 1 ? a1 : a2);
+}
+
+// Returns false for zero / non-finite directions.
+__device__ __forceinline__ bool chart_of(float d0, float d1, float d2, Chart& c)
+{
+    const float a0 = fabsf(d0), a1 = fabsf(d1), a2 = fabsf(d2);
+    int k = 0;
+    float m = a0;
+    if (a1 > m) { k = 1; m = a1; }
+    if (a2 > m) { k = 2; m = a2; }
+    if (!(m > 0.0f) || !(m <= 3.402823466e38f) || !(a0 == a0) || !(a1 == a1) || !(a2 == a2))
+        return false;
+    c.k = k;
+    c.k1 = (k == 2) ? 0 : k + 1;
+    c.k2 = (k == 0) ? 2 : k - 1;
+    const float dk = pick3(k, d0, d1, d2);
+    c.sigma = (dk < 0.0f) ? -1.0f : 1.0f;
+    c.f = 2 * k + (dk < 0.0f ? 1 : 0);
+    c.m = m;
+    c.x = __fdiv_rn(pick3(c.k1, d0, d1, d2), m);
+    c.y = __fdiv_rn(pick3(c.k2, d0, d1, d2), m);
+    return true;
+}
+
+// Cell index and local coordinate along one chart axis: x = uN + 1/2 = q N/2 + (N+1)/2 with
+// q = num/m, i = clamp(floor(x), 0, N), s = x - i, in double-float arithmetic.
+__device__ __forceinline__ void cell_of(float num, float m, int N, int& i, float& s)
+{
+    const float q = __fdiv_rn(num, m);
+    const float qe = fmaf(-q, m, num);          // exact residual of the quotient
+    const float ql = __fdiv_rn(qe, m);
+    const float hN = 0.5f * (float)N;
+    const float X = __fmul_rn(q, hN);
+    const float Xl = fmaf(q, hN, -X) + ql * hN; // product error + low part of q
+    const float c = 0.5f * (float)(N + 1);
+    float fl = floorf(__fadd_rn(X, c));
+    float sv = __fadd_rn(__fsub_rn(X, fl - c), Xl);
+    if (sv < 0.0f) { fl -= 1.0f; sv += 1.0f; }
+    else if (sv >= 1.0f) { fl += 1.0f; sv -= 1.0f; }
+    if (fl < 0.0f) { fl = 0.0f; }
+    if (fl > (float)N) { fl = (float)N; }
+    i = (int)fl;
+    s = sv;
+}
+
+// ------------------------------------------------------------------------------------------
+// Record fetch: the four corners (i,j) (i+1,j) (i,j+1) (i+1,j+1) as float4 (r, ru h, rv h, ruv h^2)
+struct Corners {
+    float4 c00, c10, c01, c11;
+};
+
+__device__ __forceinline__ float4 h4_to_f4(uint2 v)
+{
+    const __half2 a = *reinterpret_cast<const __half2*>(&v.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&v.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+__device__ __forceinline__ float4 b4_to_f4(uint2 v)
+{
+    // bf16 -> f32 is exact: the bf16 bits are the top half of the f32 bits
+    return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                       __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+}
+
+template <int DT>
+__device__ __forceinline__ float4 load_rec(const void* base, int64_t rec)
+{
+    if (DT == SHM_F32) {
+        return __ldg(reinterpret_cast<const float4*>(base) + rec);
+    } else {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(base) + rec);
+        return DT == SHM_F16 ? h4_to_f4(v) : b4_to_f4(v);
+    }
+}
+
+template <int DT, int LAYOUT>
+__device__ __forceinline__ Corners fetch_corners(const void* data, const GlyphRef& G, int f, int i, int j)
+{
+    Corners c;
+    if (LAYOUT == SHM_LAYOUT_TEXEL) {
+        const int64_t P = G.N + 2;
+        const int64_t r = G.base + ((int64_t)f * P + j) * P + i;
+        c.c00 = load_rec<DT>(data, r);
+        c.c10 = load_rec<DT>(data, r + 1);
+        c.c01 = load_rec<DT>(data, r + P);
+        c.c11 = load_rec<DT>(data, r + P + 1);
+    } else {
+        const int64_t P = G.N + 1;
+        const int64_t r = (G.base + ((int64_t)f * P + j) * P + i) * 4;  // 4 texel records per cell
+        c.c00 = load_rec<DT>(data, r);
+        c.c10 = load_rec<DT>(data, r + 1);
+        c.c01 = load_rec<DT>(data, r + 2);
+        c.c11 = load_rec<DT>(data, r + 3);
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------------------------------
+// 1-D cubic Hermite basis (§3.3) with H0 = 1 - H1 used implicitly (difference form)
+struct Herm {
+    float H1, h0d, h1d;     // H1, H0d, H1d
+    float dH1, dh0d, dh1d;  // derivatives; dH0 = -dH1
+};
+
+__device__ __forceinline__ Herm herm(float s)
+{
+    Herm h;
+    const float s2 = s * s;
+    const float om = 1.0f - s;
+    h.H1 = s2 * (3.0f - 2.0f * s);
+    h.h0d = s * om * om;
+    h.h1d = s2 * (s - 1.0f);
+    h.dH1 = 6.0f * s * om;
+    h.dh0d = om * (1.0f - 3.0f * s);
+    h.dh1d = s * (3.0f * s - 2.0f);
+    return h;
+}
+
+struct HermOut {
+    float r, rs, rt;  // value and d/ds, d/dt
+};
+
+// Tensor-product Hermite value and first derivatives from the four corner records.
+__device__ __forceinline__ HermOut hermite2(const Corners& c, float s, float t)
+{
+    const Herm a = herm(s), b = herm(t);
+    // rows along s: value row p_b and v-derivative row q_b (Hermite of r_v h with r_uv h^2)
+    const float d0 = c.c10.x - c.c00.x, d1 = c.c11.x - c.c01.x;
+    const float e0 = c.c10.z - c.c00.z, e1 = c.c11.z - c.c01.z;
+    const float p0 = c.c00.x + a.H1 * d0 + a.h0d * c.c00.y + a.h1d * c.c10.y;
+    const float p1 = c.c01.x + a.H1 * d1 + a.h0d * c.c01.y + a.h1d * c.c11.y;
+    const float q0 = c.c00.z + a.H1 * e0 + a.h0d * c.c00.w + a.h1d * c.c10.w;
+    const float q1 = c.c01.z + a.H1 * e1 + a.h0d * c.c01.w + a.h1d * c.c11.w;
+    const float ps0 = a.dH1 * d0 + a.dh0d * c.c00.y + a.dh1d * c.c10.y;
+    const float ps1 = a.dH1 * d1 + a.dh0d * c.c01.y + a.dh1d * c.c11.y;
+    const float qs0 = a.dH1 * e0 + a.dh0d * c.c00.w + a.dh1d * c.c10.w;
+    const float qs1 = a.dH1 * e1 + a.dh0d * c.c01.w + a.dh1d * c.c11.w;
+    HermOut o;
+    const float dp = p1 - p0;
+    o.r = p0 + b.H1 * dp + b.h0d * q0 + b.h1d * q1;
+    o.rs = ps0 + b.H1 * (ps1 - ps0) + b.h0d * qs0 + b.h1d * qs1;
+    o.rt = b.dH1 * dp + b.dh0d * q0 + b.dh1d * q1;
+    return o;
+}
+
+// ------------------------------------------------------------------------------------------
+// §3.4: the Cramer solution of G [alpha beta]^T = [R_u R_v]^T in closed form.  With
+// w~ = a + x b + y c, rho = |w~|, e1 = (2/rho)(I - w w^T) b, e2 = (2/rho)(I - w w^T) c, the
+// tangent vector (rho/2) [R_u b + R_v c - (x R_u + y R_v) a] satisfies grad.e1 = R_u,
+// grad.e2 = R_v and grad.w = 0, so it is alpha e1 + beta e2 (det G = 16/rho^6 > 0, no clamp).
+struct Vec3 {
+    float x, y, z;
+};
+
+__device__ __forceinline__ Vec3 s2_gradient(const Chart& c, float Ru, float Rv)
+{
+    const float rho = sqrtf(fmaf(c.x, c.x, fmaf(c.y, c.y, 1.0f)));
+    const float h = 0.5f * rho;
+    const float gk = -h * c.sigma * fmaf(c.x, Ru, c.y * Rv);
+    const float g1 = h * Ru;
+    const float g2 = h * Rv;
+    // scatter (k, k1, k2) -> (0, 1, 2)
+    Vec3 g;
+    g.x = (c.k == 0) ? gk : (c.k1 == 0 ? g1 : g2);
+    g.y = (c.k == 1) ? gk : (c.k1 == 1 ? g1 : g2);
+    g.z = (c.k == 2) ? gk : (c.k1 == 2 ? g1 : g2);
+    return g;
+}
+
+__device__ __forceinline__ Vec3 surface_normal(float d0, float d1, float d2, float R, const Vec3& g)
+{
+    const float il = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    const float mx = fmaf(R * d0, il, -g.x), my = fmaf(R * d1, il, -g.y), mz = fmaf(R * d2, il, -g.z);
+    const float im = rsqrtf(fmaf(mx, mx, fmaf(my, my, mz * mz)));
+    return Vec3{mx * im, my * im, mz * im};
+}
+
+// One full query on one glyph: returns false (and leaves outputs unset) for invalid directions.
+struct QueryResult {
+    float R, Ru, Rv;
+    Vec3 grad;
+    int f, i, j;
+};
+
+template <int DT, int LAYOUT>
+__device__ __forceinline__ bool query_one(const LutView& L, const GlyphRef& G, float d0, float d1, float d2,
+                                          QueryResult& out, Chart& c)
+{
+    if (!chart_of(d0, d1, d2, c)) return false;
+    int i, j;
+    float s, t;
+    cell_of(pick3(c.k1, d0, d1, d2), c.m, G.N, i, s);
+    cell_of(pick3(c.k2, d0, d1, d2), c.m, G.N, j, t);
+    const Corners cr = fetch_corners<DT, LAYOUT>(L.data, G, c.f, i, j);
+    const HermOut h = hermite2(cr, s, t);
+    out.R = G.r0 + h.r;
+    out.Ru = (float)G.N * h.rs;
+    out.Rv = (float)G.N * h.rt;
+    out.grad = s2_gradient(c, out.Ru, out.Rv);
+    out.f = c.f;
+    out.i = i;
+    out.j = j;
+    return true;
+}
+
+}  // namespace shm

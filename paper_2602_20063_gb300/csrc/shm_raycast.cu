@@ -1,0 +1,316 @@
+// Ray casting of star-shaped objects x(w) = c + s|r(w)| w through their Hermite tables
+// (arXiv 2602.20063, §3.1; shading normals §3.4).
+//
+// The paper renders billboards through a raster pipeline; here there is no raster stage:
+//   k_rank_objects  orders objects front to back by |c - eye| - R_max (rank by counting);
+//   k_bin_tiles     one thread per 16x16 pixel tile walks the ordered objects and keeps those
+//                   whose conservative screen rectangle (from the bounding sphere) covers it;
+//   k_raycast       persistent CTAs take tiles from an atomic counter (no waits); per pixel and
+//                   candidate object: bounding-sphere chord [t_min, t_max] -> `march` samples of
+//                   F(x) = |x - c| - R(w) -> first sign change -> `bisect` halvings -> `newton`
+//                   Newton steps with F' = d.(w - grad_{S^2}R/|x - c|) -> nearest hit -> normal
+//                   n = (R w - grad R)/|R w - grad R| with grad R = s sign(r) grad r -> Blinn-Phong.
+// Workspace: 64-byte header {uint32 tile counter, uint32 pad, uint64 surface queries evaluated},
+// then ranks [n_obj], ordered ids [n_obj], per-tile counts [tiles], per-tile lists [tiles][n_obj].
+#include <math.h>
+
+#include "shm_internal.h"
+
+namespace shm {
+
+constexpr int RT = 16;  // tile edge in pixels
+
+struct WsLayout {
+    int64_t rank_off, order_off, count_off, list_off, total;
+};
+
+__host__ __device__ __forceinline__ WsLayout ws_layout(int n_obj, int W, int H)
+{
+    const int64_t tiles = (int64_t)((W + RT - 1) / RT) * ((H + RT - 1) / RT);
+    WsLayout w;
+    w.rank_off = 64;
+    w.order_off = w.rank_off + 4LL * n_obj;
+    w.count_off = w.order_off + 4LL * n_obj;
+    w.list_off = w.count_off + 4LL * tiles;
+    w.list_off = (w.list_off + 15) / 16 * 16;
+    w.total = w.list_off + 4LL * tiles * n_obj;
+    return w;
+}
+
+int64_t raycast_workspace_bytes(int n_obj, int W, int H) { return ws_layout(n_obj, W, H).total; }
+
+__device__ __forceinline__ float depth_key(const shm_object& o, const shm_camera& cam)
+{
+    const float dx = o.centre[0] - cam.eye[0], dy = o.centre[1] - cam.eye[1], dz = o.centre[2] - cam.eye[2];
+    return sqrtf(dx * dx + dy * dy + dz * dz) - o.rmax;
+}
+
+__global__ void k_rank_objects(const shm_object* __restrict__ objs, int n, shm_camera cam, int32_t* order)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // NaN keys sort last (treated as +inf, ties by index), so ranks stay a permutation of 0..n-1
+    float ki = depth_key(objs[i], cam);
+    if (!(ki == ki)) ki = __int_as_float(0x7f800000);
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+        float kj = depth_key(objs[j], cam);
+        if (!(kj == kj)) kj = __int_as_float(0x7f800000);
+        rank += (kj < ki) || (kj == ki && j < i);
+    }
+    order[rank] = i;
+}
+
+// Conservative pixel rectangle of a sphere (centre c, radius r): for every point p of the
+// sphere, (p.right)/(p.fwd) and (p.up)/(p.fwd) lie in the box of the extreme ratios.
+__device__ __forceinline__ bool sphere_rect(const shm_object& o, const shm_camera& cam, int& x0, int& x1, int& y0,
+                                            int& y1)
+{
+    const float dx = o.centre[0] - cam.eye[0], dy = o.centre[1] - cam.eye[1], dz = o.centre[2] - cam.eye[2];
+    const float cz = dx * cam.fwd[0] + dy * cam.fwd[1] + dz * cam.fwd[2];
+    const float cx = dx * cam.right[0] + dy * cam.right[1] + dz * cam.right[2];
+    const float cy = dx * cam.up[0] + dy * cam.up[1] + dz * cam.up[2];
+    const float r = o.rmax * 1.001f + 1e-6f;
+    if (cz + r <= 0.0f) return false;  // entirely behind the camera
+    if (cz - r <= 1e-6f) {             // straddles the eye plane: cover the screen
+        x0 = 0; y0 = 0; x1 = cam.W - 1; y1 = cam.H - 1;
+        return true;
+    }
+    const float zn = cz - r, zf = cz + r;
+    const float xa = cx - r, xb = cx + r, ya = cy - r, yb = cy + r;
+    const float xmin = xa < 0.0f ? xa / zn : xa / zf, xmax = xb > 0.0f ? xb / zn : xb / zf;
+    const float ymin = ya < 0.0f ? ya / zn : ya / zf, ymax = yb > 0.0f ? yb / zn : yb / zf;
+    const float sx = 1.0f / (cam.tan_half_fov_y * ((float)cam.W / (float)cam.H)), sy = 1.0f / cam.tan_half_fov_y;
+    // px + 1/2 = (x_ndc + 1) W/2, py + 1/2 = (1 - y_ndc) H/2
+    const float fx0 = (xmin * sx + 1.0f) * 0.5f * cam.W - 0.5f, fx1 = (xmax * sx + 1.0f) * 0.5f * cam.W - 0.5f;
+    const float fy0 = (1.0f - ymax * sy) * 0.5f * cam.H - 0.5f, fy1 = (1.0f - ymin * sy) * 0.5f * cam.H - 0.5f;
+    if (fx1 < -1.0f || fy1 < -1.0f || fx0 > cam.W || fy0 > cam.H) return false;
+    x0 = max(0, (int)floorf(fx0) - 1);
+    x1 = min(cam.W - 1, (int)ceilf(fx1) + 1);
+    y0 = max(0, (int)floorf(fy0) - 1);
+    y1 = min(cam.H - 1, (int)ceilf(fy1) + 1);
+    return x0 <= x1 && y0 <= y1;
+}
+
+__global__ void k_bin_tiles(const shm_object* __restrict__ objs, int n, shm_camera cam, const int32_t* __restrict__ order,
+                            int32_t* counts, int32_t* lists)
+{
+    const int tx_n = (cam.W + RT - 1) / RT, ty_n = (cam.H + RT - 1) / RT;
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= tx_n * ty_n) return;
+    const int tx = tile % tx_n, ty = tile / tx_n;
+    const int px0 = tx * RT, px1 = min(cam.W - 1, px0 + RT - 1), py0 = ty * RT, py1 = min(cam.H - 1, py0 + RT - 1);
+    int cnt = 0;
+    int32_t* out = lists + (int64_t)tile * n;
+    for (int q = 0; q < n; ++q) {
+        const int id = __ldg(order + q);
+        if (id < 0 || id >= n) continue;
+        const shm_object o = objs[id];
+        int x0, x1, y0, y1;
+        if (!sphere_rect(o, cam, x0, x1, y0, y1)) continue;
+        if (x1 < px0 || x0 > px1 || y1 < py0 || y0 > py1) continue;
+        out[cnt++] = id;
+    }
+    counts[tile] = cnt;
+}
+
+struct Surf {
+    float F, dF;
+    float R, sgn;
+    Vec3 grad;
+};
+
+template <int DT, int LAYOUT>
+__device__ __forceinline__ bool surface_F(const LutView& L, const GlyphRef& G, float scale, const float* c, const float* o,
+                                          const Vec3& d, float t, Surf& S)
+{
+    const float x0 = o[0] + t * d.x - c[0], x1 = o[1] + t * d.y - c[1], x2 = o[2] + t * d.z - c[2];
+    QueryResult qr;
+    Chart ch;
+    if (!query_one<DT, LAYOUT>(L, G, x0, x1, x2, qr, ch)) return false;
+    const float dist = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+    S.sgn = qr.R >= 0.0f ? 1.0f : -1.0f;
+    S.R = scale * fabsf(qr.R);
+    S.F = dist - S.R;
+    S.grad = Vec3{scale * S.sgn * qr.grad.x, scale * S.sgn * qr.grad.y, scale * S.sgn * qr.grad.z};
+    const float id = 1.0f / dist;
+    const float dw = (d.x * x0 + d.y * x1 + d.z * x2) * id;
+    const float dg = d.x * S.grad.x + d.y * S.grad.y + d.z * S.grad.z;
+    S.dF = dw - dg * id;
+    return true;
+}
+
+template <int DT, int LAYOUT>
+__global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object* __restrict__ objs, int n, shm_camera cam,
+                                                    shm_raycast_params prm, const int32_t* __restrict__ counts,
+                                                    const int32_t* __restrict__ lists, uint32_t* tile_counter,
+                                                    unsigned long long* query_counter, float* rgba, float* depth,
+                                                    float* normal, int32_t* obj_id, int32_t* dev_status)
+{
+    __shared__ int s_tile;
+    const int tx_n = (cam.W + RT - 1) / RT, ty_n = (cam.H + RT - 1) / RT;
+    const int ntiles = tx_n * ty_n;
+    const float qnan = __int_as_float(0x7fc00000);
+    uint32_t status = 0;
+    unsigned long long nq = 0;
+    float lx = prm.light[0], ly = prm.light[1], lz = prm.light[2];
+    {
+        const float il = rsqrtf(lx * lx + ly * ly + lz * lz);
+        lx *= il; ly *= il; lz *= il;
+    }
+    const float aspect = (float)cam.W / (float)cam.H;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        __syncthreads();
+        if (tile >= ntiles) break;
+        const int px = (tile % tx_n) * RT + (threadIdx.x % RT), py = (tile / tx_n) * RT + (threadIdx.x / RT);
+        if (px >= cam.W || py >= cam.H) continue;
+        const float xn = (2.0f * (px + 0.5f) / cam.W - 1.0f) * cam.tan_half_fov_y * aspect;
+        const float yn = (1.0f - 2.0f * (py + 0.5f) / cam.H) * cam.tan_half_fov_y;
+        Vec3 d{cam.fwd[0] + xn * cam.right[0] + yn * cam.up[0], cam.fwd[1] + xn * cam.right[1] + yn * cam.up[1],
+               cam.fwd[2] + xn * cam.right[2] + yn * cam.up[2]};
+        {
+            const float il = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+            d.x *= il; d.y *= il; d.z *= il;
+        }
+        const float* o = cam.eye;
+        float best_t = __int_as_float(0x7f800000);
+        int best = -1;
+        const int cnt = __ldg(counts + tile);
+        const int32_t* lst = lists + (int64_t)tile * n;
+        for (int q = 0; q < cnt; ++q) {
+            const int id = __ldg(lst + q);
+            const shm_object ob = objs[id];
+            if (ob.glyph < 0 || ob.glyph >= L.n_glyphs) { status |= SHM_DEV_BOUNDS; continue; }
+            const float ocx = o[0] - ob.centre[0], ocy = o[1] - ob.centre[1], ocz = o[2] - ob.centre[2];
+            const float b = ocx * d.x + ocy * d.y + ocz * d.z;
+            const float cc = ocx * ocx + ocy * ocy + ocz * ocz - ob.rmax * ob.rmax;
+            const float disc = b * b - cc;
+            if (disc < 0.0f) continue;
+            const float sq = sqrtf(disc);
+            float t0 = -b - sq;
+            const float t1 = -b + sq;
+            if (t1 <= 0.0f) continue;
+            if (t0 < 0.0f) t0 = 0.0f;
+            if (t0 >= best_t) continue;
+            const GlyphRef G = glyph_ref(L, ob.glyph);
+            Surf S;
+            float thit = qnan;
+            if (!surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t0, S)) { status |= SHM_DEV_NONFINITE; continue; }
+            ++nq;
+            if (S.F < 0.0f) {
+                thit = t0;
+            } else {
+                float lo = t0, hi = t0;
+                bool found = false;
+                for (int k = 1; k <= prm.march; ++k) {
+                    const float tk = t0 + (t1 - t0) * (float)k / (float)prm.march;
+                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, tk, S);
+                    ++nq;
+                    if (S.F < 0.0f) {
+                        lo = t0 + (t1 - t0) * (float)(k - 1) / (float)prm.march;
+                        hi = tk;
+                        found = true;
+                        break;
+                    }
+                }
+                if (!found) continue;
+                for (int it = 0; it < prm.bisect; ++it) {
+                    const float mid = 0.5f * (lo + hi);
+                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, mid, S);
+                    ++nq;
+                    if (S.F < 0.0f) hi = mid; else lo = mid;
+                }
+                float t = 0.5f * (lo + hi);
+                for (int it = 0; it < prm.newton; ++it) {
+                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t, S);
+                    ++nq;
+                    if (S.dF == 0.0f) break;
+                    const float tn = t - S.F / S.dF;
+                    if (!(tn >= lo && tn <= hi)) break;
+                    t = tn;
+                }
+                thit = t;
+            }
+            if (thit < best_t) {
+                best_t = thit;
+                best = id;
+            }
+        }
+        const int64_t pix = (int64_t)py * cam.W + px;
+        if (best < 0) {
+            if (rgba) { rgba[4 * pix] = 0.f; rgba[4 * pix + 1] = 0.f; rgba[4 * pix + 2] = 0.f; rgba[4 * pix + 3] = 0.f; }
+            if (depth) depth[pix] = __int_as_float(0x7f800000);
+            if (normal) { normal[3 * pix] = 0.f; normal[3 * pix + 1] = 0.f; normal[3 * pix + 2] = 0.f; }
+            if (obj_id) obj_id[pix] = -1;
+            continue;
+        }
+        const shm_object ob = objs[best];
+        const GlyphRef G = glyph_ref(L, ob.glyph);
+        Surf S;
+        surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, best_t, S);
+        ++nq;
+        const float x0 = o[0] + best_t * d.x - ob.centre[0], x1 = o[1] + best_t * d.y - ob.centre[1],
+                    x2 = o[2] + best_t * d.z - ob.centre[2];
+        const Vec3 n = surface_normal(x0, x1, x2, S.R, S.grad);
+        float hx = lx - d.x, hy = ly - d.y, hz = lz - d.z;
+        const float ih = rsqrtf(hx * hx + hy * hy + hz * hz);
+        hx *= ih; hy *= ih; hz *= ih;
+        const float ndl = n.x * lx + n.y * ly + n.z * lz;
+        const float ndh = n.x * hx + n.y * hy + n.z * hz;
+        const float I = prm.ambient + prm.kd * fmaxf(ndl, 0.0f) + prm.ks * (ndh > 0.0f ? powf(ndh, prm.shininess) : 0.0f);
+        if (rgba) { rgba[4 * pix] = I; rgba[4 * pix + 1] = I; rgba[4 * pix + 2] = I; rgba[4 * pix + 3] = 1.0f; }
+        if (depth) depth[pix] = best_t;
+        if (normal) { normal[3 * pix] = n.x; normal[3 * pix + 1] = n.y; normal[3 * pix + 2] = n.z; }
+        if (obj_id) obj_id[pix] = best;
+    }
+    for (int off = 16; off > 0; off >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, off);
+    if ((threadIdx.x & 31) == 0 && nq) atomicAdd(query_counter, nq);
+    report_status(dev_status, status);
+}
+
+cudaError_t launch_raycast(const LutView& L, const shm_object* objs, int n_obj, const shm_camera& cam,
+                           const shm_raycast_params& prm, float* rgba, float* depth, float* normal, int32_t* obj_id,
+                           void* ws, size_t ws_bytes, int32_t* dev_status, cudaStream_t s)
+{
+    (void)ws_bytes;
+    const WsLayout w = ws_layout(n_obj, cam.W, cam.H);
+    char* base = (char*)ws;
+    int32_t* order = (int32_t*)(base + w.order_off);
+    int32_t* counts = (int32_t*)(base + w.count_off);
+    int32_t* lists = (int32_t*)(base + w.list_off);
+    const int tiles = ((cam.W + RT - 1) / RT) * ((cam.H + RT - 1) / RT);
+    cudaError_t e = cudaMemsetAsync(base, 0, 64, s);
+    if (e != cudaSuccess) return e;
+    if (n_obj > 0) {
+        e = cudaMemsetAsync(order, 0xff, 4LL * n_obj, s);
+        if (e != cudaSuccess) return e;
+        k_rank_objects<<<(n_obj + 127) / 128, 128, 0, s>>>(objs, n_obj, cam, order);
+        k_bin_tiles<<<(tiles + 127) / 128, 128, 0, s>>>(objs, n_obj, cam, order, counts, lists);
+    } else {
+        e = cudaMemsetAsync(counts, 0, 4LL * tiles, s);
+        if (e != cudaSuccess) return e;
+    }
+    int blocks = sm_count() * 4;
+    if (blocks > tiles) blocks = tiles;
+    uint32_t* tile_counter = (uint32_t*)base;
+    unsigned long long* qc = (unsigned long long*)(base + 8);
+#define SHM_RC(DT, LY)                                                                                         \
+    k_raycast<DT, LY><<<blocks, RT * RT, 0, s>>>(L, objs, n_obj, cam, prm, counts, lists, tile_counter, qc, rgba, \
+                                                 depth, normal, obj_id, dev_status)
+    if (L.layout == SHM_LAYOUT_TEXEL) {
+        if (L.dtype == SHM_F32) SHM_RC(SHM_F32, SHM_LAYOUT_TEXEL);
+        else if (L.dtype == SHM_F16) SHM_RC(SHM_F16, SHM_LAYOUT_TEXEL);
+        else SHM_RC(SHM_BF16, SHM_LAYOUT_TEXEL);
+    } else {
+        if (L.dtype == SHM_F32) SHM_RC(SHM_F32, SHM_LAYOUT_CELL);
+        else if (L.dtype == SHM_F16) SHM_RC(SHM_F16, SHM_LAYOUT_CELL);
+        else SHM_RC(SHM_BF16, SHM_LAYOUT_CELL);
+    }
+#undef SHM_RC
+    return cudaGetLastError();
+}
+
+}  // namespace shm

@@ -1,0 +1,103 @@
+"""GPU parity of the adjoint (shm_query_backward, shm_build_lut_backward) against the FP64 oracle.
+
+Tolerances: dlut is a float32 atomic sum of per-query contributions, so each entry is compared
+within 2e-5 of its channel's largest magnitude; ddirs involves the Hermite second derivatives
+scaled by N^2 and is compared within 1e-4 of its largest magnitude, away from cell edges (the
+patch is only C^1 there, so the one-sided second derivative depends on the chosen cell).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import shm_inputs as I
+from gpu_common import near_edge, shm, upload_pool
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    return shm()
+
+
+def _case(seed, N=10, L=4, Q=8192, c00=2.0):
+    c = I.sh_coeffs(1, L, seed)[0]
+    c[0] += c00
+    lut = O.bake_sh(N, L, c)
+    dirs = I.directions(Q, seed + 1)
+    rng = np.random.default_rng(seed)
+    gR = rng.normal(size=Q).astype(np.float32)
+    gG = rng.normal(size=(Q, 3)).astype(np.float32)
+    gn = rng.normal(size=(Q, 3)).astype(np.float32)
+    return lut, dirs, gR, gG, gn
+
+
+@pytest.mark.parametrize("dtype,layout", [(0, 0), (0, 1), (2, 0)])
+def test_query_backward_parity(S, dtype, layout):
+    N = 10
+    lut, dirs, gR, gG, gn = _case(40, N)
+    r0 = np.array([0.3], np.float32)
+    L, stored = upload_pool(S, [lut], r0=r0, dtype=dtype, layout=layout)
+    dl = S.like_lut(L, dtype=0, layout=0, zero=True)
+    t = lambda a: torch.from_numpy(a).cuda()
+    ddirs = S.query_backward(L, t(dirs), dl, gR=t(gR), ggrad=t(gG), gnormal=t(gn))
+    dref, ddref = O.query_vjp(stored.reshape(-1, 4), [0], [N], dirs, gR=gR, gG=gG, gn=gn, r0=r0.astype(np.float64))
+    got = dl.data.view(-1, 4).double().cpu().numpy()
+    for ch in range(4):
+        scale = np.abs(dref[:, ch]).max()
+        assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * scale, ch
+    ok = ~near_edge(None, dirs, [N], None, eps=1e-4)
+    dd = ddirs.double().cpu().numpy()
+    scale = np.abs(ddref[ok]).max()
+    assert np.abs(dd[ok] - ddref[ok]).max() <= 1e-4 * scale
+
+
+def test_backward_accumulates_and_segments(S):
+    luts = [O.bake_sh(n, 6, I.sh_coeffs(1, 6, 70 + n)[0] + np.eye(1, 49, 0)[0] * 2.0) for n in (4, 12, 31)]
+    L, stored = upload_pool(S, luts)
+    counts = np.array([100, 0, 3001])
+    Q = int(counts.sum())
+    dirs = I.directions(Q, 71)
+    seg = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    glyph = np.repeat(np.arange(3), counts).astype(np.int32)
+    rng = np.random.default_rng(72)
+    gR = rng.normal(size=Q).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    dl = S.like_lut(L, zero=True)
+    S.query_backward(L, t(dirs), dl, gR=t(gR), seg=t(seg), want_ddirs=False)
+    S.query_backward(L, t(dirs), dl, gR=t(gR), seg=t(seg), want_ddirs=False)  # accumulates (+=)
+    off, Ns = O.make_pool(luts)[1:]
+    dref, _ = O.query_vjp(stored.reshape(-1, 4), off, Ns, dirs, gR=gR, glyph=glyph, want_ddirs=False)
+    got = dl.data.view(-1, 4).double().cpu().numpy()
+    assert np.abs(got - 2 * dref).max() <= 4e-5 * np.abs(2 * dref).max()
+
+
+def test_dot_product_on_device(S):
+    N = 12
+    rng = np.random.default_rng(73)
+    X = rng.normal(size=(6, N + 2, N + 2, 4))
+    L, stored = upload_pool(S, [X])
+    dirs = I.directions(20000, 74)
+    y = rng.normal(size=20000).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    JX = S.query(L, t(dirs), want=("R",))["R"].double()
+    dl = S.like_lut(L, zero=True)
+    S.query_backward(L, t(dirs), dl, gR=t(y), want_ddirs=False)
+    lhs = float((JX * t(y).double()).sum())
+    rhs = float((L.data.double() * dl.data.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1.0)
+
+
+@pytest.mark.parametrize("N,L,G", [(10, 4, 1), (32, 8, 40)])
+def test_build_backward(S, N, L, G):
+    rng = np.random.default_rng(N)
+    T = 6 * (N + 2) ** 2
+    dlut = rng.normal(size=(G, T * 4)).astype(np.float32)
+    basis = S.sh_basis(N, L)
+    D = S.alloc_lut(G, N)
+    D.data.copy_(torch.from_numpy(dlut.ravel()))
+    dc = S.build_lut_backward(D, L, basis).double().cpu().numpy()
+    for g in range(min(G, 6)):
+        ref = O.bake_sh_vjp(N, L, dlut[g].astype(np.float64).reshape(6, N + 2, N + 2, 4))
+        assert np.abs(dc[g] - ref).max() <= 2e-5 * np.abs(ref).max()

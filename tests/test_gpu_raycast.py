@@ -1,0 +1,170 @@
+"""GPU parity of shm_raycast against the FP64 oracle ray caster (§3.1).
+
+Several results can be correct where a march sample of F lies within rounding of 0: a float32
+and a float64 evaluation may then bracket different roots.  The oracle reports, per pixel, the
+smallest |F| over its march samples; pixels with margin < 1e-4 R_max are excluded from the exact
+comparison of hit object, and must stay a small fraction.  Elsewhere: identical object ids, depth
+within 2e-5 relative (bisection + Newton in float32), normals and shading within 2e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import shm_inputs as I
+from gpu_common import shm, upload_pool
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    return shm()
+
+
+def camera_frame(eye, target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0)):
+    eye = np.asarray(eye, dtype=np.float64)
+    fwd = np.asarray(target) - eye
+    fwd /= np.linalg.norm(fwd)
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    upv = np.cross(right, fwd)
+    return eye, fwd, right, upv
+
+
+def _scene(n_obj, seed, choices=(16, 32)):
+    counts, offs, mu, amp, width = I.bump_params(n_obj, seed)
+    Ns = I.uneven_N(n_obj, seed + 1, choices=choices)
+    luts = []
+    for o in range(n_obj):
+        s = slice(offs[o], offs[o + 1])
+        luts.append(O.bake_fd(int(Ns[o]), O.sample_grid_bumps(int(Ns[o]), mu[s], amp[s], width[s]), r0=1.0))
+    return luts, Ns
+
+
+def _run(S, luts, centres, scale, W, H, eye, fov=45.0, prm_kw=None):
+    n = len(luts)
+    r0 = np.ones(n, np.float32)
+    L, stored = upload_pool(S, luts, r0=r0)
+    rmax_dev = S.lut_bounds(L).cpu().numpy() * np.asarray(scale, np.float32)
+    objs = S.objects_tensor(centres, scale, rmax_dev, np.arange(n))
+    eye, fwd, right, up = camera_frame(eye)
+    cam = S.make_camera(eye, fwd, right, up, fov, W, H)
+    prm = S.make_raycast_params(**(prm_kw or {}))
+    out = S.raycast(L, objs, n, cam, prm)
+    torch.cuda.synchronize()
+    pool = stored.reshape(-1, 4)
+    off, Ns = O.make_pool(luts)[1:]
+    rmax_o = np.array([O.lut_bound(pool[off[g]:off[g] + 6 * (Ns[g] + 2) ** 2].reshape(6, Ns[g] + 2, Ns[g] + 2, 4),
+                                   int(Ns[g]), 1.0) for g in range(n)]) * np.asarray(scale)
+    ocam = O.make_camera(eye, fwd, right, up, fov, W, H)
+    oprm = O.make_raycast_params(**(prm_kw or {}))
+    ref = O.raycast(pool, off, Ns, centres, scale, rmax_o, np.arange(n), ocam, oprm, r0=r0.astype(np.float64))
+    return out, ref, rmax_o
+
+
+def _compare(out, ref, rmax, W, H):
+    ids = out["obj_id"].cpu().numpy().reshape(-1)
+    depth = out["depth"].double().cpu().numpy().reshape(-1)
+    nrm = out["normal"].double().cpu().numpy().reshape(-1, 3)
+    rgba = out["rgba"].double().cpu().numpy().reshape(-1, 4)
+    amb = ref["margin"] < 1e-4 * rmax.max()
+    same = ids == ref["obj_id"]
+    assert np.all(same[~amb]), np.nonzero(~same & ~amb)[0][:10]
+    assert amb.mean() < 0.01
+    hit = same & (ids >= 0) & ~amb
+    assert hit.sum() > 0.05 * W * H
+    rel = np.abs(depth[hit] - ref["depth"][hit]) / ref["depth"][hit]
+    assert rel.max() <= 2e-5, rel.max()
+    assert np.abs(nrm[hit] - ref["normal"][hit]).max() <= 2e-3
+    assert np.abs(rgba[hit] - ref["rgba"][hit]).max() <= 2e-3
+    miss = same & (ids < 0)
+    assert np.all(np.isinf(depth[miss]))
+    return hit.sum()
+
+
+def test_sphere_closed_form(S):
+    N = 8
+    lut = np.zeros((6, N + 2, N + 2, 4))
+    lut[..., 0] = 0.0
+    L, _ = upload_pool(S, [lut], r0=np.array([1.0], np.float32))
+    objs = S.objects_tensor([[0.3, -0.2, 0.0]], [1.2], [1.5], [0])
+    eye, fwd, right, up = camera_frame((0.0, 0.0, 6.0))
+    W, H = 64, 48
+    cam = S.make_camera(eye, fwd, right, up, 40.0, W, H)
+    out = S.raycast(L, objs, 1, cam, S.make_raycast_params())
+    depth = out["depth"].double().cpu().numpy()
+    th = math.tan(math.radians(20.0))
+    c = np.array([0.3, -0.2, 0.0])
+    n_hit = 0
+    for py in range(H):
+        for px in range(W):
+            xn = (2 * (px + 0.5) / W - 1) * th * W / H
+            yn = (1 - 2 * (py + 0.5) / H) * th
+            d = fwd + xn * right + yn * up
+            d /= np.linalg.norm(d)
+            oc = eye - c
+            b = oc @ d
+            disc = b * b - (oc @ oc - 1.44)
+            if disc < 1e-4:
+                continue
+            t = -b - math.sqrt(disc)
+            assert abs(depth[py, px] - t) <= 2e-5 * t
+            n_hit += 1
+    assert n_hit > 100
+
+
+def test_bump_scene_parity(S):
+    luts, Ns = _scene(8, 300)
+    centres = np.array([[x, y, z] for x in (-1.6, 1.6) for y in (-1.6, 1.6) for z in (-1.6, 1.6)])
+    out, ref, rmax = _run(S, luts, centres, np.ones(8), 96, 64, eye=(2.5, 3.0, 9.0))
+    _compare(out, ref, rmax, 96, 64)
+
+
+def test_sampled_pixels_full_size_grid(S):
+    """8x8x8 grid of 512 objects at 1920x1080 (the impostor workload): sampled pixels vs the oracle."""
+    n = 512
+    luts, Ns = _scene(n, 20063 + 2, choices=(16, 32, 64, 128))
+    g = (np.arange(8) - 3.5) * 3.0
+    centres = np.array([[x, y, z] for x in g for y in g for z in g])
+    r0 = np.ones(n, np.float32)
+    L, stored = upload_pool(S, luts, r0=r0)
+    rmax = S.lut_bounds(L).cpu().numpy()
+    objs = S.objects_tensor(centres, np.ones(n), rmax, np.arange(n))
+    R_scene = math.sqrt(3) * 10.5 + float(rmax.max())
+    dist = R_scene / math.sin(math.radians(22.5))
+    eye, fwd, right, up = camera_frame((0.0, 0.0, dist))
+    W, H = 1920, 1080
+    cam = S.make_camera(eye, fwd, right, up, 45.0, W, H)
+    out = S.raycast(L, objs, n, cam, S.make_raycast_params())
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    px = rng.integers(0, W, 400).astype(np.int32)
+    py = rng.integers(0, H, 400).astype(np.int32)
+    pool = stored.reshape(-1, 4)
+    off, Nn = O.make_pool(luts)[1:]
+    rmax_o = np.array([O.lut_bound(pool[off[k]:off[k] + 6 * (Nn[k] + 2) ** 2].reshape(6, Nn[k] + 2, Nn[k] + 2, 4),
+                                   int(Nn[k]), 1.0) for k in range(n)])
+    ref = O.raycast(pool, off, Nn, centres, np.ones(n), rmax_o, np.arange(n),
+                    O.make_camera(eye, fwd, right, up, 45.0, W, H), O.make_raycast_params(), px=px, py=py,
+                    r0=r0.astype(np.float64))
+    ids = out["obj_id"].cpu().numpy()[py, px]
+    depth = out["depth"].double().cpu().numpy()[py, px]
+    amb = ref["margin"] < 1e-4 * rmax_o.max()
+    assert np.all((ids == ref["obj_id"])[~amb])
+    hit = (ids >= 0) & ~amb
+    assert hit.sum() > 50
+    assert (np.abs(depth[hit] - ref["depth"][hit]) / ref["depth"][hit]).max() <= 2e-5
+    assert S.raycast_query_count(out["_ws"]) > 0
+
+
+def test_workspace_too_small(S):
+    lut = np.zeros((6, 6, 6, 4))
+    L, _ = upload_pool(S, [lut], r0=np.array([1.0], np.float32))
+    objs = S.objects_tensor([[0, 0, 0]], [1.0], [1.0], [0])
+    eye, fwd, right, up = camera_frame((0.0, 0.0, 5.0))
+    cam = S.make_camera(eye, fwd, right, up, 40.0, 32, 32)
+    with pytest.raises(S.ShmError):
+        S.raycast(L, objs, 1, cam, S.make_raycast_params(), ws=torch.empty(16, dtype=torch.uint8, device="cuda"))
