@@ -139,20 +139,31 @@ typedef struct {
     int32_t octaves;
     const uint32_t* keys;
     float base_freq, lacunarity, gain, amplitude;
+    int32_t* dev_status; /* optional device status word (SHM_DEV_TIMEOUT from the tensor-core bake) */
 } shm_source;
 
-/* Bytes of the SH bake basis for resolution N and degree L (host). */
+/* Bytes of the SH bake basis for resolution N and degree L (host): K = (L+1)^2, M = 4*6(N+2)^2
+ * table scalars per glyph, Kp = K rounded up to a multiple of 32; 4 * (K*M + 2*M*Kp). */
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
 
 /* Fills `basis` (device, shm_sh_basis_bytes) with every real SH function's record
  * (Y, Y_u h, Y_v h, Y_uv h^2) at every stored texel of the padded cubemap, from analytic
  * derivatives converted to the chart by the chain rule (§3.3, Algorithm 1).  The bake of
- * coefficients c is then lut = sum_k c_k basis_k.  Compute once per (N, L) and reuse. */
+ * coefficients c is then lut = sum_k c_k basis_k.  Layout (float32): full [K][M] (row k =
+ * basis_k's table, texel-major, channel innermost), then hi [M][Kp] and lo [M][Kp] with
+ * hi = tf32(full^T), lo = tf32(full^T - hi), zero for k >= K (operands of the tensor-core bake).
+ * Compute once per (N, L) and reuse. */
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream);
+
+/* Workspace bytes that select the tensor-core engine of shm_build_lut for (lut, src): for SH
+ * sources 2 * n_glyphs * Kp * 4 (tf32 hi/lo split of the coefficients); 0 for other sources. */
+int64_t shm_build_workspace_bytes(const shm_lut* lut, const shm_source* src);
 
 /* Writes every record of every glyph of `lut` (any dtype/layout) from `src` (Algorithm 1:
  * gutter texels evaluated at their own centres, derivative channels in each face's chart).
- * ws/ws_bytes: workspace, may be NULL/0 (no current source needs one). */
+ * SH sources: with ws != NULL and ws_bytes >= shm_build_workspace_bytes the contraction runs on
+ * the tensor cores (tcgen05, 3xTF32 split, float32-grade accuracy); with ws == NULL on the
+ * float32 CUDA cores.  A non-NULL ws smaller than required returns SHM_ERR_WORKSPACE. */
 shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, size_t ws_bytes,
                          shm_stream stream);
 
@@ -181,6 +192,22 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
  * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L). */
 shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis,
                                   float* dcoeffs, shm_stream stream);
+
+/* Fused fit loss and adjoint (not in the paper; fits tables to targets).  Per query the forward
+ * of shm_query is recomputed and L_q = w_value (R - R_target)^2 + w_normal |n - n_target|^2 is
+ * formed; sum_q L_q is added (+=) to *loss (device float, may be NULL) and dL/d(stored record) is
+ * accumulated (+=) into dlut (float32 texel layout, same glyphs and resolutions as lut).
+ * R_target [Q], n_target [Q][3] float32.  Same glyph selection as shm_query. */
+shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
+                            const int64_t* seg, const float* R_target, const float* n_target,
+                            float w_value, float w_normal, const shm_lut* dlut, float* loss,
+                            int32_t* dev_status, shm_stream stream);
+
+/* One Adam step (Kingma & Ba 2015) over n float32 parameters with bias correction at step `step`
+ * (>= 1): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps).
+ * zero_grad != 0 also sets grad to 0 for the next accumulation. */
+shm_status shm_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, int32_t zero_grad, shm_stream stream);
 
 /* ---------------------------------------------------------------- direct SH (ground truth) */
 

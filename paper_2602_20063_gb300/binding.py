@@ -41,7 +41,7 @@ class c_source(C.Structure):
                 ("samples", C.c_void_p), ("sample_offset", C.c_void_p), ("bump_offset", C.c_void_p),
                 ("mu", C.c_void_p), ("amp", C.c_void_p), ("width", C.c_void_p), ("octaves", C.c_int32),
                 ("keys", C.c_void_p), ("base_freq", C.c_float), ("lacunarity", C.c_float), ("gain", C.c_float),
-                ("amplitude", C.c_float)]
+                ("amplitude", C.c_float), ("dev_status", C.c_void_p)]
 
 
 class c_camera(C.Structure):
@@ -69,10 +69,13 @@ _SIGS = {
     "shm_sh_basis_bytes": (C.c_int64, [_I32, _I32]),
     "shm_sh_basis": (C.c_int, [_I32, _I32, _VP, _VP]),
     "shm_build_lut": (C.c_int, [_VP, _VP, _VP, _SZ, _VP]),
+    "shm_build_workspace_bytes": (C.c_int64, [_VP, _VP]),
     "shm_pack_lut": (C.c_int, [_VP, _VP, _VP]),
     "shm_lut_bounds": (C.c_int, [_VP, _VP, _VP]),
     "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "shm_fit_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
+    "shm_adam_step": (C.c_int, [_VP, _VP, _VP, _VP, _I64, C.c_float, C.c_float, C.c_float, C.c_float, _I32, _I32, _VP]),
     "shm_sh_eval": (C.c_int, [_I32, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_raycast_workspace_bytes": (C.c_int64, [_I32, _I32, _I32]),
     "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
@@ -268,19 +271,33 @@ class Source:
     lacunarity: float = 2.0
     gain: float = 0.5
     amplitude: float = 0.02
+    dev_status: torch.Tensor = None
 
     def c(self) -> c_source:
         s = c_source()
         s.kind, s.L, s.octaves = self.kind, self.L, self.octaves
-        for name in ("coeffs", "basis", "samples", "sample_offset", "bump_offset", "mu", "amp", "width", "keys"):
+        for name in ("coeffs", "basis", "samples", "sample_offset", "bump_offset", "mu", "amp", "width", "keys",
+                     "dev_status"):
             t = getattr(self, name)
             setattr(s, name, t.data_ptr() if t is not None else None)
         s.base_freq, s.lacunarity, s.gain, s.amplitude = self.base_freq, self.lacunarity, self.gain, self.amplitude
         return s
 
 
-def build_lut(lut: Lut, src: Source, stream=None):
-    _check(lib().shm_build_lut(C.byref(lut.c()), C.byref(src.c()), None, 0, _stream(stream)), "shm_build_lut")
+def build_workspace_bytes(lut: Lut, src: Source) -> int:
+    return int(lib().shm_build_workspace_bytes(C.byref(lut.c()), C.byref(src.c())))
+
+
+def build_lut(lut: Lut, src: Source, ws: torch.Tensor = None, stream=None):
+    """shm_build_lut.  For SH sources a workspace of build_workspace_bytes selects the tensor-core
+    engine; ws=None runs the float32 CUDA-core engine."""
+    wp, wn = (None, 0) if ws is None else (_ptr(ws), ws.numel() * ws.element_size())
+    _check(lib().shm_build_lut(C.byref(lut.c()), C.byref(src.c()), wp, wn, _stream(stream)), "shm_build_lut")
+
+
+def build_workspace(lut: Lut, src: Source) -> torch.Tensor:
+    n = build_workspace_bytes(lut, src)
+    return torch.empty(max(n, 16), dtype=torch.uint8, device=lut.data.device)
 
 
 def pack_lut(src: Lut, dst: Lut, stream=None):
@@ -314,6 +331,29 @@ def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None) -> t
     _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc), _stream(stream)),
            "shm_build_lut_backward")
     return dc
+
+
+def fit_backward(lut: Lut, dirs: torch.Tensor, R_target: torch.Tensor, n_target: torch.Tensor, dlut: Lut,
+                 w_value: float = 1.0, w_normal: float = 1.0, loss: torch.Tensor = None, glyph=None, seg=None,
+                 dev_status=None, stream=None):
+    """shm_fit_backward: accumulates dL/dtable into dlut and sum_q L_q into loss (device float [1])."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    _need(R_target, torch.float32, (Q,), "R_target")
+    _need(n_target, torch.float32, (Q, 3), "n_target")
+    st = lib().shm_fit_backward(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(R_target),
+                                _ptr(n_target), float(w_value), float(w_normal), C.byref(dlut.c()), _ptr(loss),
+                                _ptr(dev_status), _stream(stream))
+    _check(st, "shm_fit_backward")
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, zero_grad: bool = True, stream=None):
+    for t, nm in ((param, "param"), (grad, "grad"), (m, "m"), (v, "v")):
+        _need(t, torch.float32, (param.numel(),) if t.dim() == 1 else None, nm)
+    st = lib().shm_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr), float(beta1),
+                             float(beta2), float(eps), int(step), int(bool(zero_grad)), _stream(stream))
+    _check(st, "shm_adam_step")
 
 
 # ------------------------------------------------------------------------------------------- direct SH

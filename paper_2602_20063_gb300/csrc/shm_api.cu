@@ -133,19 +133,28 @@ shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
 {
     if (N < 1 || L < 0 || L > 20) return -1;
-    return (int64_t)(L + 1) * (L + 1) * 6 * (N + 2) * (N + 2) * 4 * (int64_t)sizeof(float);
+    const int64_t K = (int64_t)(L + 1) * (L + 1), M = 4LL * 6 * (N + 2) * (N + 2);
+    return (K * M + 2 * M * sh_kpad(L)) * (int64_t)sizeof(float);
 }
 
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream)
 {
     if (N < 1 || N > (1 << 14) || L < 0 || L > 20 || !basis) return SHM_ERR_INVALID_ARG;
-    return map_cuda(launch_sh_basis(N, L, basis, (cudaStream_t)stream));
+    cudaError_t e = launch_sh_basis(N, L, basis, (cudaStream_t)stream);
+    if (e != cudaSuccess) return SHM_ERR_CUDA;
+    return map_cuda(launch_basis_split(N, L, basis, (cudaStream_t)stream));
+}
+
+int64_t shm_build_workspace_bytes(const shm_lut* lut, const shm_source* src)
+{
+    if (!lut || !src || lut->n_glyphs <= 0) return -1;
+    if (src->kind != SHM_SRC_SH) return 0;
+    if (src->L < 0 || src->L > 20) return -1;
+    return sh_build_workspace_bytes(lut->n_glyphs, src->L);
 }
 
 shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, size_t ws_bytes, shm_stream stream)
 {
-    (void)ws;
-    (void)ws_bytes;
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
     if (!src) return SHM_ERR_INVALID_ARG;
@@ -155,6 +164,11 @@ shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, si
     case SHM_SRC_SH:
         if (lut->N_uniform <= 0) return SHM_ERR_UNSUPPORTED;
         if (src->L < 0 || src->L > 20 || !src->coeffs || !src->basis) return SHM_ERR_INVALID_ARG;
+        if (ws) {
+            if ((int64_t)ws_bytes < sh_build_workspace_bytes(lut->n_glyphs, src->L) || ((uintptr_t)ws & 15u))
+                return SHM_ERR_WORKSPACE;
+            return map_cuda(launch_sh_build_tc(v, lut->data, src->L, src->coeffs, src->basis, ws, s, src->dev_status));
+        }
         return map_cuda(launch_sh_build(v, lut->data, src->L, src->coeffs, src->basis, s));
     case SHM_SRC_SAMPLES:
     case SHM_SRC_BUMPS:
@@ -223,7 +237,51 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, 
     a.gnormal = gnormal;
     a.ddirs = ddirs;
     a.dev_status = dev_status;
+    a.fit = 0;
+    a.R_target = a.n_target = nullptr;
+    a.w_value = a.w_normal = 0.0f;
+    a.loss = nullptr;
     return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
+}
+
+shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
+                            const int64_t* seg, const float* R_target, const float* n_target, float w_value,
+                            float w_normal, const shm_lut* dlut, float* loss, int32_t* dev_status, shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    st = check_lut(dlut);
+    if (st != SHM_OK) return st;
+    if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
+    if (dlut->n_glyphs != lut->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if (Q < 0 || (Q > 0 && (!dirs || !R_target || !n_target))) return SHM_ERR_INVALID_ARG;
+    BackwardArgs a;
+    a.L = view(lut);
+    a.D = view(dlut);
+    a.dlut = (float*)dlut->data;
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = glyph;
+    a.seg = glyph ? nullptr : seg;
+    a.gR = a.ggrad = a.gnormal = nullptr;
+    a.ddirs = nullptr;
+    a.dev_status = dev_status;
+    a.fit = 1;
+    a.R_target = R_target;
+    a.n_target = n_target;
+    a.w_value = w_value;
+    a.w_normal = w_normal;
+    a.loss = loss;
+    return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
+}
+
+shm_status shm_adam_step(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                         float eps, int32_t step, int32_t zero_grad, shm_stream stream)
+{
+    if (n < 0 || (n > 0 && (!param || !grad || !m || !v)) || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return SHM_ERR_INVALID_ARG;
+    return map_cuda(launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, zero_grad, (cudaStream_t)stream));
 }
 
 shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis, float* dcoeffs,

@@ -1,0 +1,440 @@
+// Tensor-core SH bake (arXiv 2602.20063, Algorithm 1 with analytic SH derivatives, §3.3) on the
+// 5th-generation tensor cores of sm_103a: tcgen05.mma with TMEM accumulators, operands staged by
+// TMA into 128-byte-swizzled shared memory.
+//
+// The bake of G glyphs is the contraction
+//     table[g][c] = sum_k coeff[g][k] basis[c][k]            (c = texel * 4 + channel, 4T columns)
+// computed transposed, D[c][g] = A[c][:] . B[g][:], so that TMEM lane = table column and TMEM column =
+// glyph: each epilogue thread owns one table column and a warp's 32 lanes store 32 consecutive
+// floats of one glyph's table (coalesced 128 B).
+//
+// Precision: kind::tf32 multiplies 10-bit-mantissa operands.  To stay at float32 accuracy both
+// operands are split x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi), round to nearest) and
+//     D = A_hi B_hi + A_hi B_lo + A_lo B_hi      (the 3xTF32 scheme of Ootomo & Yokota, 2022),
+// leaving a relative error ~2^-21 per product, below the float32 accumulation error of K terms.
+//
+// Schedule: persistent CTAs (one per SM, 256 threads), tiles of 128 columns x 256 glyphs, K in
+// chunks of 32 (128 B rows, the swizzle atom), 2 smem stages of 96 KB, 2 TMEM accumulators of 256
+// columns (512 columns, the whole TMEM) so the epilogue of one tile overlaps the MMAs of the next.
+//   warp 0 lane 0: TMA producer        warp 1: TMEM allocation; lane 0 issues the MMAs
+//   warps 4-7: epilogue (TMEM lane quadrant = warp % 4), table writes
+// Every mbarrier wait is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, drains its own
+// copies and MMAs with bounded waits, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "shm_internal.h"
+
+namespace shm {
+namespace tc {
+
+constexpr int TM = 128;  // table columns per tile (MMA M)
+constexpr int TN = 256;  // glyphs per tile (MMA N)
+constexpr int KC = 32;   // K per stage: 32 x 4 B = one 128-byte swizzle row
+constexpr int NSTAGE = 2;
+constexpr uint32_t A_BYTES = TM * KC * 4;
+constexpr uint32_t B_BYTES = TN * KC * 4;
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr uint32_t BAR_BYTES = 256;
+constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;   // 1 s
+constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;   // 100 ms
+
+// kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major, N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+struct Args {
+    int M;                // table columns, 4T
+    int G;                // glyphs
+    int Kp;               // padded K (multiple of 32)
+    float* out;           // f32 texel table [G][M] when direct
+    LutView view;         // output table (any dtype / layout) for the generic epilogue
+    void* data;
+    int direct;           // 1: f32 texel layout, uniform N, write out[g*M + c]
+    int32_t* dev_status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete.  Returns false after `limit` ns or as
+// soon as another role has raised the abort flag.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > limit) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 B (SBO).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;      // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_sh_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, Args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* bars = smem + NSTAGE * STAGE_BYTES;
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NSTAGE, tfull0 = empty0 + 8 * NSTAGE,
+                   tempty0 = tfull0 + 16, drain = tempty0 + 16;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 128);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 136);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_m = (a.M + TM - 1) / TM, num_n = (a.G + TN - 1) / TN;
+    const int tiles = num_m * num_n;
+    const int NC = a.Kp / KC;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(tfull0 + 8 * q, 1);
+            mbar_init(tempty0 + 8 * q, 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        uint32_t it = 0;
+        int issued[NSTAGE] = {0, 0};
+        bool ok = true;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const int mt = t % num_m, nt = t / num_m;
+            for (int c = 0; c < NC; ++c, ++it) {
+                const int s = it % NSTAGE;
+                const uint32_t ph = (it / NSTAGE) & 1;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+                uint8_t* st = smem + s * STAGE_BYTES;
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, STAGE_BYTES);
+                tma_load_2d(smem_u32(st), &mAh, c * KC, mt * TM, fb);
+                tma_load_2d(smem_u32(st + A_BYTES), &mAl, c * KC, mt * TM, fb);
+                tma_load_2d(smem_u32(st + 2 * A_BYTES), &mBh, c * KC, nt * TN, fb);
+                tma_load_2d(smem_u32(st + 2 * A_BYTES + B_BYTES), &mBl, c * KC, nt * TN, fb);
+                issued[s] = (int)(it / NSTAGE) + 1;
+            }
+        }
+        if (!ok) {
+            // drain: the last load issued into each stage must land before the CTA exits
+            for (int s = 0; s < NSTAGE; ++s)
+                if (issued[s] > 0) {
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)(issued[s] - 1) & 1) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
+                    }
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        uint32_t it = 0, j = 0;
+        bool ok = true, any = false;
+        for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++j) {
+            const uint32_t acc = j & 1, aph = (j >> 1) & 1;
+            if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+            fence_after();
+            const uint32_t d = tmem + acc * TN;
+            for (int c = 0; c < NC; ++c, ++it) {
+                const int s = it % NSTAGE;
+                const uint32_t ph = (it / NSTAGE) & 1;
+                if (!mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+                fence_after();
+                const uint32_t ah = smem_u32(smem + s * STAGE_BYTES), al = ah + A_BYTES;
+                const uint32_t bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < KC / 8; ++kk) {
+                    const uint32_t o = kk * 32;  // 8 tf32 = 32 B along K inside the swizzle row
+                    mma_tf32(d, sdesc(ah + o), sdesc(bh + o), (c | kk) != 0);
+                    mma_tf32(d, sdesc(ah + o), sdesc(bl + o), 1);
+                    mma_tf32(d, sdesc(al + o), sdesc(bh + o), 1);
+                }
+                any = true;
+                mma_commit(empty0 + 8 * s);
+            }
+            if (!ok) break;
+            mma_commit(tfull0 + 8 * acc);
+        }
+        if (!ok && any) {
+            mma_commit(drain);
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
+            }
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- epilogue
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        uint32_t j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            const int mt = t % num_m, nt = t / num_m;
+            const uint32_t acc = j & 1, aph = (j >> 1) & 1;
+            if (!mbar_wait(tfull0 + 8 * acc, aph, abort_flag, WAIT_LIMIT_NS)) break;
+            fence_after();
+            const int col = mt * TM + row;
+            const bool col_ok = col < a.M;
+            const int ch = col & 3;
+            for (int n0 = 0; n0 < TN; n0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TN + n0, r);
+                const int g0 = nt * TN + n0;
+                if (a.direct) {
+#pragma unroll 8
+                    for (int i = 0; i < 32; ++i) {
+                        const int g = g0 + i;
+                        if (g < a.G && col_ok) {
+                            float v = __uint_as_float(r[i]);
+                            if (ch == 0 && a.view.r0) v -= __ldg(a.view.r0 + g);
+                            a.out[(int64_t)g * a.M + col] = v;
+                        }
+                    }
+                } else {
+                    // gather the four channels of a texel into the lane holding channel 0
+                    const int P = a.view.N_uniform + 2;
+                    const int tex = col >> 2;
+                    const int f = tex / (P * P), rem = tex % (P * P), jj = rem / P, ii = rem % P;
+                    for (int i = 0; i < 32; ++i) {
+                        const float v0 = __uint_as_float(r[i]);
+                        const float v1 = __shfl_down_sync(0xffffffffu, v0, 1);
+                        const float v2 = __shfl_down_sync(0xffffffffu, v0, 2);
+                        const float v3 = __shfl_down_sync(0xffffffffu, v0, 3);
+                        const int g = g0 + i;
+                        if (ch == 0 && g < a.G && col_ok) {
+                            const GlyphRef Gr = glyph_ref(a.view, g);
+                            store_texel(a.data, a.view.dtype, a.view.layout, Gr, f, jj, ii,
+                                        make_float4(v0 - Gr.r0, v1, v2, v3));
+                        }
+                    }
+                }
+            }
+            fence_before();
+            mbar_arrive(tempty0 + 8 * acc);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag && a.dev_status) atomicOr(a.dev_status, SHM_DEV_TIMEOUT);
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// tf32 round-to-nearest (ties away) of a float: the tensor cores read the top 19 bits.
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// rows x K float32 (row stride ld_in) -> hi, lo [rows][Kp] (zero padded)
+__global__ void k_split_rows(const float* __restrict__ in, int rows, int K, int64_t ld_in, int64_t col_stride,
+                             int Kp, float* __restrict__ hi, float* __restrict__ lo)
+{
+    const int64_t n = (int64_t)rows * Kp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / Kp;
+        const int k = (int)(e % Kp);
+        const float v = (k < K) ? __ldg(in + r * col_stride + (int64_t)k * ld_in) : 0.0f;
+        const float h = tf32_rna(v);
+        hi[e] = h;
+        lo[e] = tf32_rna(v - h);
+    }
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+static EncodeFn encode_fn()
+{
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, const float* base, int rows, int Kp, int box_rows)
+{
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+int sh_kpad(int L) { return (((L + 1) * (L + 1) + tc::KC - 1) / tc::KC) * tc::KC; }
+
+int64_t sh_build_workspace_bytes(int G, int L) { return 2LL * G * sh_kpad(L) * (int64_t)sizeof(float); }
+
+// basis: [K][M] float32 (full), followed by hi [M][Kp] and lo [M][Kp]
+cudaError_t launch_basis_split(int N, int L, float* basis, cudaStream_t s)
+{
+    const int K = (L + 1) * (L + 1), Kp = sh_kpad(L), M = 4 * 6 * (N + 2) * (N + 2);
+    float* hi = basis + (int64_t)K * M;
+    float* lo = hi + (int64_t)M * Kp;
+    const int64_t n = (int64_t)M * Kp;
+    tc::k_split_rows<<<(unsigned)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8), 256, 0, s>>>(
+        basis, M, K, (int64_t)M, 1, Kp, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const float* coeffs, const float* basis,
+                               void* ws, cudaStream_t s, int32_t* dev_status)
+{
+    const int N = out.N_uniform, G = out.n_glyphs;
+    const int K = (L + 1) * (L + 1), Kp = sh_kpad(L), M = 4 * 6 * (N + 2) * (N + 2);
+    float* chi = reinterpret_cast<float*>(ws);
+    float* clo = chi + (int64_t)G * Kp;
+    const int64_t n = (int64_t)G * Kp;
+    tc::k_split_rows<<<(unsigned)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8), 256, 0, s>>>(
+        coeffs, G, K, 1, (int64_t)K, Kp, chi, clo);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const float* bhi = basis + (int64_t)K * M;
+    const float* blo = bhi + (int64_t)M * Kp;
+    CUtensorMap mAh, mAl, mBh, mBl;
+    if (!tc::make_map(&mAh, bhi, M, Kp, tc::TM) || !tc::make_map(&mAl, blo, M, Kp, tc::TM) ||
+        !tc::make_map(&mBh, chi, G, Kp, tc::TN) || !tc::make_map(&mBl, clo, G, Kp, tc::TN))
+        return cudaErrorInvalidValue;
+    tc::Args a;
+    a.M = M;
+    a.G = G;
+    a.Kp = Kp;
+    a.view = out;
+    a.data = data;
+    a.out = reinterpret_cast<float*>(data);
+    a.direct = (out.dtype == SHM_F32 && out.layout == SHM_LAYOUT_TEXEL) ? 1 : 0;
+    a.dev_status = dev_status;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(tc::k_sh_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    const int tiles = ((M + tc::TM - 1) / tc::TM) * ((G + tc::TN - 1) / tc::TN);
+    int grid = sm_count();
+    if (grid > tiles) grid = tiles;
+    tc::k_sh_gemm_tc<<<grid, 256, tc::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
+    return cudaGetLastError();
+}
+
+}  // namespace shm

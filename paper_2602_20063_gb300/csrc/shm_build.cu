@@ -187,66 +187,6 @@ cudaError_t launch_sh_basis(int N, int L, float* basis, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------------------------------
-// Generic record store / load for any dtype and layout.
-__device__ __forceinline__ uint2 f4_to_h4(float4 v)
-{
-    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
-}
-
-__device__ __forceinline__ uint2 f4_to_b4(float4 v)
-{
-    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
-    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
-}
-
-__device__ __forceinline__ void store_rec(void* data, int dtype, int64_t rec, float4 v)
-{
-    if (dtype == SHM_F32) reinterpret_cast<float4*>(data)[rec] = v;
-    else if (dtype == SHM_F16) reinterpret_cast<uint2*>(data)[rec] = f4_to_h4(v);
-    else reinterpret_cast<uint2*>(data)[rec] = f4_to_b4(v);
-}
-
-__device__ __forceinline__ float4 load_rec_any(const void* data, int dtype, int64_t rec)
-{
-    if (dtype == SHM_F32) return load_rec<SHM_F32>(data, rec);
-    if (dtype == SHM_F16) return load_rec<SHM_F16>(data, rec);
-    return load_rec<SHM_BF16>(data, rec);
-}
-
-// Store texel (i, j) of face f: one record (texel layout) or up to four cell corners.
-__device__ __forceinline__ void store_texel(void* data, int dtype, int layout, const GlyphRef& G, int f, int j,
-                                            int i, float4 v)
-{
-    if (layout == SHM_LAYOUT_TEXEL) {
-        const int64_t P = G.N + 2;
-        store_rec(data, dtype, G.base + ((int64_t)f * P + j) * P + i, v);
-    } else {
-        const int64_t P = G.N + 1;
-        for (int cj = j - 1; cj <= j; ++cj) {
-            if (cj < 0 || cj > G.N) continue;
-            for (int ci = i - 1; ci <= i; ++ci) {
-                if (ci < 0 || ci > G.N) continue;
-                const int corner = (j - cj) * 2 + (i - ci);
-                store_rec(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + corner, v);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float4 load_texel(const void* data, int dtype, int layout, const GlyphRef& G, int f,
-                                             int j, int i)
-{
-    if (layout == SHM_LAYOUT_TEXEL) {
-        const int64_t P = G.N + 2;
-        return load_rec_any(data, dtype, G.base + ((int64_t)f * P + j) * P + i);
-    }
-    const int64_t P = G.N + 1;
-    const int ci = min(i, G.N), cj = min(j, G.N);
-    return load_rec_any(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + (j - cj) * 2 + (i - ci));
-}
-
-// ------------------------------------------------------------------------------------------
 // SIMT bake contraction: tile of 32 glyphs x 64 texels (x 4 channels), K in chunks of 16.
 constexpr int GT_G = 32, GT_T = 64, GT_K = 16;
 

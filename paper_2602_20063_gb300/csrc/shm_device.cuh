@@ -66,6 +66,7 @@ struct Chart {
     int k, k1, k2;   // dominant axis and the two chart axes
     float sigma;     // sign of d_k
     float m;         // |d_k|
+    float im;        // 1/|d_k| (round to nearest)
     float x, y;      // chart coordinates 2u-1 = d_k1/|d_k|, 2v-1 = d_k2/|d_k|
     int f;           // face 2k + (d_k < 0)
 };
@@ -75,7 +76,8 @@ __device__ __forceinline__ float pick3(int c, float a0, float a1, float a2)
     return c == 0 ? a0 : (c == 1 ? a1 : a2);
 }
 
-// Returns false for zero / non-finite directions.
+// Returns false for zero / non-finite directions.  Besides the face it keeps 1/|d_k| so the
+// cell coordinates need no further division.
 __device__ __forceinline__ bool chart_of(float d0, float d1, float d2, Chart& c)
 {
     const float a0 = fabsf(d0), a1 = fabsf(d1), a2 = fabsf(d2);
@@ -92,21 +94,23 @@ __device__ __forceinline__ bool chart_of(float d0, float d1, float d2, Chart& c)
     c.sigma = (dk < 0.0f) ? -1.0f : 1.0f;
     c.f = 2 * k + (dk < 0.0f ? 1 : 0);
     c.m = m;
-    c.x = __fdiv_rn(pick3(c.k1, d0, d1, d2), m);
-    c.y = __fdiv_rn(pick3(c.k2, d0, d1, d2), m);
+    c.im = __frcp_rn(m);
+    c.x = pick3(c.k1, d0, d1, d2) * c.im;
+    c.y = pick3(c.k2, d0, d1, d2) * c.im;
     return true;
 }
 
 // Cell index and local coordinate along one chart axis: x = uN + 1/2 = q N/2 + (N+1)/2 with
-// q = num/m, i = clamp(floor(x), 0, N), s = x - i, in double-float arithmetic.
-__device__ __forceinline__ void cell_of(float num, float m, int N, int& i, float& s)
+// q = num/m, i = clamp(floor(x), 0, N), s = x - i, in double-float arithmetic: q = q0 + q1 with
+// q0 = num * (1/m) and q1 = fma(-q0, m, num) * (1/m) (the residual is exact), carried through
+// X = q N/2 with its exact product error, so s is correct to ~1e-8 of a cell for any N < 2^20.
+__device__ __forceinline__ void cell_of(float num, float m, float im, int N, int& i, float& s)
 {
-    const float q = __fdiv_rn(num, m);
-    const float qe = fmaf(-q, m, num);          // exact residual of the quotient
-    const float ql = __fdiv_rn(qe, m);
+    const float q = num * im;
+    const float ql = fmaf(-q, m, num) * im;
     const float hN = 0.5f * (float)N;
     const float X = __fmul_rn(q, hN);
-    const float Xl = fmaf(q, hN, -X) + ql * hN; // product error + low part of q
+    const float Xl = fmaf(q, hN, -X) + ql * hN;  // product error + low part of q
     const float c = 0.5f * (float)(N + 1);
     float fl = floorf(__fadd_rn(X, c));
     float sv = __fadd_rn(__fsub_rn(X, fl - c), Xl);
@@ -266,8 +270,8 @@ __device__ __forceinline__ bool query_one(const LutView& L, const GlyphRef& G, f
     if (!chart_of(d0, d1, d2, c)) return false;
     int i, j;
     float s, t;
-    cell_of(pick3(c.k1, d0, d1, d2), c.m, G.N, i, s);
-    cell_of(pick3(c.k2, d0, d1, d2), c.m, G.N, j, t);
+    cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, G.N, i, s);
+    cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, G.N, j, t);
     const Corners cr = fetch_corners<DT, LAYOUT>(L.data, G, c.f, i, j);
     const HermOut h = hermite2(cr, s, t);
     out.R = G.r0 + h.r;
@@ -278,6 +282,66 @@ __device__ __forceinline__ bool query_one(const LutView& L, const GlyphRef& G, f
     out.i = i;
     out.j = j;
     return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Generic record store / load for any dtype and layout.
+__device__ __forceinline__ uint2 f4_to_h4(float4 v)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+__device__ __forceinline__ uint2 f4_to_b4(float4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
+__device__ __forceinline__ void store_rec(void* data, int dtype, int64_t rec, float4 v)
+{
+    if (dtype == SHM_F32) reinterpret_cast<float4*>(data)[rec] = v;
+    else if (dtype == SHM_F16) reinterpret_cast<uint2*>(data)[rec] = f4_to_h4(v);
+    else reinterpret_cast<uint2*>(data)[rec] = f4_to_b4(v);
+}
+
+__device__ __forceinline__ float4 load_rec_any(const void* data, int dtype, int64_t rec)
+{
+    if (dtype == SHM_F32) return load_rec<SHM_F32>(data, rec);
+    if (dtype == SHM_F16) return load_rec<SHM_F16>(data, rec);
+    return load_rec<SHM_BF16>(data, rec);
+}
+
+// Store texel (i, j) of face f: one record (texel layout) or up to four cell corners.
+__device__ __forceinline__ void store_texel(void* data, int dtype, int layout, const GlyphRef& G, int f, int j,
+                                            int i, float4 v)
+{
+    if (layout == SHM_LAYOUT_TEXEL) {
+        const int64_t P = G.N + 2;
+        store_rec(data, dtype, G.base + ((int64_t)f * P + j) * P + i, v);
+    } else {
+        const int64_t P = G.N + 1;
+        for (int cj = j - 1; cj <= j; ++cj) {
+            if (cj < 0 || cj > G.N) continue;
+            for (int ci = i - 1; ci <= i; ++ci) {
+                if (ci < 0 || ci > G.N) continue;
+                const int corner = (j - cj) * 2 + (i - ci);
+                store_rec(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + corner, v);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float4 load_texel(const void* data, int dtype, int layout, const GlyphRef& G, int f,
+                                             int j, int i)
+{
+    if (layout == SHM_LAYOUT_TEXEL) {
+        const int64_t P = G.N + 2;
+        return load_rec_any(data, dtype, G.base + ((int64_t)f * P + j) * P + i);
+    }
+    const int64_t P = G.N + 1;
+    const int ci = min(i, G.N), cj = min(j, G.N);
+    return load_rec_any(data, dtype, (G.base + ((int64_t)f * P + cj) * P + ci) * 4 + (j - cj) * 2 + (i - ci));
 }
 
 }  // namespace shm

@@ -35,14 +35,27 @@ struct BackwardArgs {
     const float* gnormal;
     float* ddirs;
     int32_t* dev_status;
+    // fused fit loss (fit != 0): upstream gradients from L = sum_q w_v (R - R_t)^2 + w_n |n - n_t|^2
+    int fit;
+    const float* R_target;
+    const float* n_target;
+    float w_value, w_normal;
+    float* loss;  // accumulated (+=) sum of the per-query losses
 };
 
 int sm_count();
 
 cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s);
 cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s);
+cudaError_t launch_adam(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                        float eps, int step, int zero_grad, cudaStream_t s);
 
 cudaError_t launch_sh_basis(int N, int L, float* basis, cudaStream_t s);
+cudaError_t launch_basis_split(int N, int L, float* basis, cudaStream_t s);
+cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const float* coeffs, const float* basis,
+                               void* ws, cudaStream_t s, int32_t* dev_status);
+int sh_kpad(int L);
+int64_t sh_build_workspace_bytes(int G, int L);
 cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* coeffs, const float* basis,
                             cudaStream_t s);
 cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,

@@ -12,9 +12,10 @@ namespace shm {
 
 constexpr int QCHUNK = 8;
 constexpr int QBLOCK = 256;
+constexpr int QMINBLOCKS = 5;  // <= 51 registers: 40 resident warps per SM
 
 template <int DT, int LAYOUT>
-__global__ void __launch_bounds__(QBLOCK) k_query_fwd(QueryArgs a)
+__global__ void __launch_bounds__(QBLOCK, QMINBLOCKS) k_query_fwd(QueryArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * QBLOCK + threadIdx.x) >> 5;
@@ -25,27 +26,45 @@ __global__ void __launch_bounds__(QBLOCK) k_query_fwd(QueryArgs a)
     const float qnan = __int_as_float(0x7fc00000);
 
     for (int64_t c0 = warp0 * chunk; c0 < a.Q; c0 += nwarps * chunk) {
+        // glyph of the chunk's first query and the end of its segment (one search per chunk)
         int g = 0;
+        int64_t seg_end = INT64_MAX;
         if (a.seg) {
             int g0 = 0;
-            if (lane == 0) g0 = (c0 < __ldg(a.seg)) ? -1 : seg_find(a.seg, G, c0);
+            long long e0 = 0;
+            if (lane == 0) {
+                g0 = (c0 < __ldg(a.seg)) ? -1 : seg_find(a.seg, G, c0);
+                e0 = (g0 >= 0 && g0 < G) ? __ldg(a.seg + g0 + 1) : 0;
+            }
             g = __shfl_sync(0xffffffffu, g0, 0);
+            seg_end = __shfl_sync(0xffffffffu, e0, 0);
         }
+        int64_t q = c0 + lane;
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+        if (q < a.Q) { n0 = __ldg(a.dirs + 3 * q); n1 = __ldg(a.dirs + 3 * q + 1); n2 = __ldg(a.dirs + 3 * q + 2); }
 #pragma unroll 1
-        for (int it = 0; it < QCHUNK; ++it) {
-            const int64_t q = c0 + it * 32 + lane;
+        for (int it = 0; it < QCHUNK; ++it, q += 32) {
             if (q >= a.Q) break;
+            const float d0 = n0, d1 = n1, d2 = n2;
+            // prefetch the next direction of this lane: its latency overlaps the table fetch below
+            if (it + 1 < QCHUNK && q + 32 < a.Q) {
+                n0 = __ldg(a.dirs + 3 * (q + 32));
+                n1 = __ldg(a.dirs + 3 * (q + 32) + 1);
+                n2 = __ldg(a.dirs + 3 * (q + 32) + 2);
+            }
             int gq = 0;
-            bool valid = true;
             if (a.glyph) {
                 gq = __ldg(a.glyph + q);
             } else if (a.seg) {
-                if (g < 0 && q >= __ldg(a.seg)) g = 0;
-                while (g >= 0 && g < G && q >= __ldg(a.seg + g + 1)) ++g;
+                if (q >= seg_end || g < 0) {
+                    if (g < 0 && q >= __ldg(a.seg)) g = 0;
+                    while (g >= 0 && g < G && q >= __ldg(a.seg + g + 1)) ++g;
+                    seg_end = (g >= 0 && g < G) ? __ldg(a.seg + g + 1) : INT64_MAX;
+                }
                 gq = g;
             }
+            bool valid = true;
             if (gq < 0 || gq >= G) { valid = false; status |= SHM_DEV_BOUNDS; }
-            const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
             QueryResult r;
             Chart c;
             if (valid) {
@@ -65,7 +84,7 @@ __global__ void __launch_bounds__(QBLOCK) k_query_fwd(QueryArgs a)
                 a.grad[3 * q + 2] = r.grad.z;
             }
             if (a.normal) {
-                Vec3 n = valid ? surface_normal(d0, d1, d2, r.R, r.grad) : Vec3{qnan, qnan, qnan};
+                const Vec3 n = valid ? surface_normal(d0, d1, d2, r.R, r.grad) : Vec3{qnan, qnan, qnan};
                 a.normal[3 * q] = n.x;
                 a.normal[3 * q + 1] = n.y;
                 a.normal[3 * q + 2] = n.z;
@@ -87,9 +106,17 @@ __global__ void __launch_bounds__(QBLOCK) k_query_fwd(QueryArgs a)
 template <int DT, int LAYOUT>
 static cudaError_t launch_fwd_t(const QueryArgs& a, cudaStream_t s)
 {
+    // one persistent wave: SMs x resident blocks per SM
+    static int resident = 0;
+    if (resident == 0) {
+        int r = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_query_fwd<DT, LAYOUT>, QBLOCK, 0) != cudaSuccess || r < 1)
+            r = QMINBLOCKS;
+        resident = r;
+    }
     const int64_t chunks = (a.Q + 32 * QCHUNK - 1) / (32 * QCHUNK);
     int64_t blocks = (chunks + (QBLOCK / 32) - 1) / (QBLOCK / 32);
-    const int64_t cap = (int64_t)sm_count() * 8;
+    const int64_t cap = (int64_t)sm_count() * resident;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_query_fwd<DT, LAYOUT><<<(unsigned)blocks, QBLOCK, 0, s>>>(a);

@@ -39,9 +39,10 @@ __device__ __forceinline__ Herm2 herm2(float s)
     return h;
 }
 
-template <int DT, int LAYOUT>
+template <int DT, int LAYOUT, bool FIT>
 __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
 {
+    float loss_acc = 0.0f;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * BBLOCK + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * BBLOCK) >> 5;
@@ -81,8 +82,8 @@ __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
                 const int N = Gr.N;
                 int i, j;
                 float s, t;
-                cell_of(pick3(c.k1, d0, d1, d2), c.m, N, i, s);
-                cell_of(pick3(c.k2, d0, d1, d2), c.m, N, j, t);
+                cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, N, i, s);
+                cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, N, j, t);
                 const Corners cr = fetch_corners<DT, LAYOUT>(a.L.data, Gr, c.f, i, j);
                 const Herm2 A = herm2(s), B = herm2(t);
                 // --- forward (difference form) with second derivatives
@@ -124,13 +125,26 @@ __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
                 // upstream in the (a, b, c) frame
                 float gRu_in = a.gR ? __ldg(a.gR + q) : 0.0f;
                 float gGa = 0.f, gGb = 0.f, gGc = 0.f, gna = 0.f, gnb = 0.f, gnc = 0.f;
-                if (a.ggrad) {
+                if (FIT) {
+                    // L_q = w_v (R - R_t)^2 + w_n |n - n_t|^2: upstream dL/dR, dL/dn in the frame
+                    const float eR = R - __ldg(a.R_target + q);
+                    const float t0 = __ldg(a.n_target + 3 * q), t1 = __ldg(a.n_target + 3 * q + 1),
+                                t2 = __ldg(a.n_target + 3 * q + 2);
+                    const float ea = na - pick3(c.k, t0, t1, t2) * c.sigma, eb = nb - pick3(c.k1, t0, t1, t2),
+                                ec = nc - pick3(c.k2, t0, t1, t2);
+                    loss_acc += a.w_value * eR * eR + a.w_normal * (ea * ea + eb * eb + ec * ec);
+                    gRu_in = 2.0f * a.w_value * eR;
+                    gna = 2.0f * a.w_normal * ea;
+                    gnb = 2.0f * a.w_normal * eb;
+                    gnc = 2.0f * a.w_normal * ec;
+                }
+                if (!FIT && a.ggrad) {
                     const float gx0 = __ldg(a.ggrad + 3 * q), gx1 = __ldg(a.ggrad + 3 * q + 1), gx2 = __ldg(a.ggrad + 3 * q + 2);
                     gGa = pick3(c.k, gx0, gx1, gx2) * c.sigma;
                     gGb = pick3(c.k1, gx0, gx1, gx2);
                     gGc = pick3(c.k2, gx0, gx1, gx2);
                 }
-                if (a.gnormal) {
+                if (!FIT && a.gnormal) {
                     const float gx0 = __ldg(a.gnormal + 3 * q), gx1 = __ldg(a.gnormal + 3 * q + 1), gx2 = __ldg(a.gnormal + 3 * q + 2);
                     gna = pick3(c.k, gx0, gx1, gx2) * c.sigma;
                     gnb = pick3(c.k1, gx0, gx1, gx2);
@@ -198,6 +212,10 @@ __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
             }
         }
     }
+    if (FIT) {
+        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+        if ((threadIdx.x & 31) == 0 && a.loss) atomicAdd(a.loss, loss_acc);
+    }
     report_status(a.dev_status, status);
 }
 
@@ -209,7 +227,8 @@ static cudaError_t launch_bwd_t(const BackwardArgs& a, cudaStream_t s)
     const int64_t cap = (int64_t)sm_count() * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_query_bwd<DT, LAYOUT><<<(unsigned)blocks, BBLOCK, 0, s>>>(a);
+    if (a.fit) k_query_bwd<DT, LAYOUT, true><<<(unsigned)blocks, BBLOCK, 0, s>>>(a);
+    else k_query_bwd<DT, LAYOUT, false><<<(unsigned)blocks, BBLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -225,6 +244,38 @@ cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s)
     if (dt == SHM_F32) return launch_bwd_t<SHM_F32, SHM_LAYOUT_CELL>(a, s);
     if (dt == SHM_F16) return launch_bwd_t<SHM_F16, SHM_LAYOUT_CELL>(a, s);
     return launch_bwd_t<SHM_BF16, SHM_LAYOUT_CELL>(a, s);
+}
+
+}  // namespace shm
+
+namespace shm {
+
+// Adam (Kingma & Ba, 2015) with bias correction; optionally zeroes the gradient for the next step.
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, int zero_grad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        if (zero_grad) g[i] = 0.0f;
+    }
+}
+
+cudaError_t launch_adam(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
+                        float eps, int step, int zero_grad, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const float c1 = 1.0f - (float)pow((double)beta1, (double)step);
+    const float c2 = 1.0f - (float)pow((double)beta2, (double)step);
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    k_adam<<<(unsigned)blocks, 256, 0, s>>>(param, grad, m, v, n, lr, beta1, beta2, eps, c1, c2, zero_grad);
+    return cudaGetLastError();
 }
 
 }  // namespace shm

@@ -30,45 +30,104 @@ def _rel_err(got, ref):
     return [np.abs(got[..., c] - ref[..., c]).max() / max(np.abs(ref[..., c]).max(), 1e-30) for c in range(4)]
 
 
+def _split_basis(buf, N, L):
+    K, M = (L + 1) ** 2, 4 * 6 * (N + 2) ** 2
+    Kp = (K + 31) // 32 * 32
+    full = buf[:K * M].reshape(K, M)
+    hi = buf[K * M:K * M + M * Kp].reshape(M, Kp)
+    lo = buf[K * M + M * Kp:].reshape(M, Kp)
+    return full, hi, lo, K, Kp
+
+
 @pytest.mark.parametrize("N,L", [(10, 4), (32, 8), (7, 16)])
 def test_sh_basis(S, N, L):
-    B = S.sh_basis(N, L).cpu().numpy().astype(np.float64).reshape((L + 1) ** 2, 6, N + 2, N + 2, 4)
+    buf = S.sh_basis(N, L).cpu().numpy()
+    full, hi, lo, K, Kp = _split_basis(buf, N, L)
+    B = full.astype(np.float64).reshape(K, 6, N + 2, N + 2, 4)
     ref = O.sh_basis_records(N, L)
     for c in range(4):
         scale = np.abs(ref[..., c]).max()
         err = np.abs(B[..., c] - ref[..., c]).max()
         assert err <= (4e-6 if c < 3 else 4e-5) * scale, (c, err / scale)
+    # tensor-core operands: tf32 (low 13 mantissa bits clear) hi + lo reproduces the float32 basis
+    assert np.all(hi.view(np.uint32) & 0x1FFF == 0) and np.all(lo.view(np.uint32) & 0x1FFF == 0)
+    assert np.all(hi[:, K:] == 0) and np.all(lo[:, K:] == 0)
+    fT = full.T.astype(np.float64)
+    assert np.all(np.abs(hi[:, :K] + lo[:, :K].astype(np.float64) - fT) <= 2.0 ** -21 * np.abs(fT))
 
 
-@pytest.mark.parametrize("N,L,G", [(10, 4, 1), (32, 8, 70), (12, 16, 3)])
-def test_sh_build(S, N, L, G):
+@pytest.mark.parametrize("engine", ["simt", "tcgen05"])
+@pytest.mark.parametrize("N,L,G", [(10, 4, 1), (32, 8, 70), (12, 16, 3), (9, 8, 300)])
+def test_sh_build(S, N, L, G, engine):
+    """Against the oracle bake, element by element, within the float32 summation bound of the
+    contraction, |err| <= (2^-20 + K 2^-24) sum_k |c_k| |B_k|, plus the float32 basis error that
+    test_sh_basis bounds (4e-6 of each basis function's channel range, r_uv 4e-5) times |c_k|; the tf32
+    split of the tensor-core engine contributes < 2^-21 sum_k |c_k B_k|."""
     c = I.sh_coeffs(G, L, 20063 + N)
     basis = S.sh_basis(N, L)
     r0 = np.linspace(0.0, 0.3, G).astype(np.float32)
     lut = S.alloc_lut(G, N, r0=r0)
-    S.build_lut(lut, S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=torch.from_numpy(c.astype(np.float32)).cuda(),
-                              basis=basis))
+    src = S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=torch.from_numpy(c.astype(np.float32)).cuda(), basis=basis,
+                   dev_status=torch.zeros(1, dtype=torch.int32, device="cuda"))
+    S.build_lut(lut, src, ws=S.build_workspace(lut, src) if engine == "tcgen05" else None)
+    assert src.dev_status.item() == 0
     got = lut.data.cpu().numpy().astype(np.float64).reshape(G, 6, N + 2, N + 2, 4)
-    for g in range(G):
-        ref = O.bake_sh(N, L, c[g].astype(np.float32).astype(np.float64))
+    K = (L + 1) ** 2
+    Babs = np.abs(O.sh_basis_records(N, L))
+    Bmax = Babs.max(axis=(1, 2, 3))  # [K][4]: per basis function and channel
+    worst = 0.0
+    for g in range(min(G, 8)):
+        cg = c[g].astype(np.float32).astype(np.float64)
+        ref = O.bake_sh(N, L, cg)
         ref[..., 0] -= r0[g]
-        e = _rel_err(got[g], ref)
-        assert max(e[:3]) <= 4e-6 and e[3] <= 4e-5, e
+        # contraction rounding + the float32 basis error (<= 4e-6 of each basis channel's range, 4e-5 for r_uv)
+        bound = (2.0 ** -20 + K * 2.0 ** -24) * np.tensordot(np.abs(cg), Babs, axes=1) + \
+            np.abs(cg) @ Bmax * np.array([4e-6, 4e-6, 4e-6, 4e-5])
+        err = np.abs(got[g] - ref)
+        worst = max(worst, float((err / bound).max()))
+        assert np.all(err <= bound), (g, float((err / bound).max()))
+    print(f"{engine} N={N} L={L}: worst error / bound = {worst:.3f}")
 
 
+@pytest.mark.parametrize("engine", ["simt", "tcgen05"])
 @pytest.mark.parametrize("dtype,layout", [(0, 1), (1, 0), (2, 1)])
-def test_sh_build_other_encodings(S, dtype, layout):
+def test_sh_build_other_encodings(S, dtype, layout, engine):
     """Building straight into 16-bit / cell layout equals building f32 texel then packing."""
     N, L, G = 16, 8, 5
     c = torch.from_numpy(I.sh_coeffs(G, L, 3).astype(np.float32)).cuda()
     basis = S.sh_basis(N, L)
     a = S.alloc_lut(G, N, r0=[0.5] * G)
-    S.build_lut(a, S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=c, basis=basis))
+    src = S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=c, basis=basis)
+    ws = S.build_workspace(a, src) if engine == "tcgen05" else None
+    S.build_lut(a, src, ws=ws)
     b = S.alloc_lut(G, N, dtype=dtype, layout=layout, r0=[0.5] * G)
-    S.build_lut(b, S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=c, basis=basis))
+    S.build_lut(b, src, ws=ws)
     p = S.like_lut(a, dtype=dtype, layout=layout)
     S.pack_lut(a, p)
     assert torch.equal(b.data, p.data)
+
+
+def test_tensor_core_bake_matches_cuda_core_bake(S):
+    """The full glyph-field shape (G = 16384, L = 8, N = 32): both engines within float32 rounding."""
+    N, L, G = 32, 8, 16384
+    c = torch.from_numpy(I.sh_coeffs(G, L, 20063 + 1).astype(np.float32)).cuda()
+    basis = S.sh_basis(N, L)
+    src = S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=c, basis=basis)
+    a = S.alloc_lut(G, N)
+    S.build_lut(a, src)
+    b = S.alloc_lut(G, N)
+    S.build_lut(b, src, ws=S.build_workspace(b, src))
+    A, B = a.data.view(G, -1, 4), b.data.view(G, -1, 4)
+    for ch in range(4):
+        scale = float(A[..., ch].abs().max())
+        err = float((A[..., ch] - B[..., ch]).abs().max())
+        assert err <= (4e-6 if ch < 3 else 4e-5) * scale, (ch, err / scale)
+    # sampled glyphs against the oracle
+    for g in (0, 4097, G - 1):
+        ref = O.bake_sh(N, L, c[g].double().cpu().numpy())
+        got = B[g].double().cpu().numpy().reshape(ref.shape)
+        e = _rel_err(got, ref)
+        assert max(e[:3]) <= 4e-6 and e[3] <= 4e-5, e
 
 
 def test_sh_end_to_end_query(S):
@@ -77,7 +136,8 @@ def test_sh_end_to_end_query(S):
     c32 = c.astype(np.float32)
     basis = S.sh_basis(N, L)
     lut = S.alloc_lut(G, N)
-    S.build_lut(lut, S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=torch.from_numpy(c32).cuda(), basis=basis))
+    src = S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=torch.from_numpy(c32).cuda(), basis=basis)
+    S.build_lut(lut, src, ws=S.build_workspace(lut, src))
     per = 4096
     dirs = I.directions(G * per, 78)
     seg = torch.from_numpy(I.query_glyphs_csr(G, per)).cuda()

@@ -90,3 +90,34 @@ def test_bake_vjp_is_transpose(oracle):
     lhs = (oracle.bake_sh(N, L, c) * Y).sum()
     rhs = c @ oracle.bake_sh_vjp(N, L, Y)
     assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs))
+
+
+def test_fit_loss_gradient_vs_finite_differences(oracle):
+    import oracle.fit as OF
+    N = 8
+    lut = _setup(oracle, N, seed=41)
+    pool, off, Ns = oracle.make_pool([lut])
+    dirs = I.directions(200, 42)
+    rng = np.random.default_rng(43)
+    Rt = rng.normal(size=200) * 0.1 + 0.7
+    nt = rng.normal(size=(200, 3))
+    nt /= np.linalg.norm(nt, axis=1, keepdims=True)
+    loss, g = OF.loss_and_grad(pool, off, Ns, dirs, Rt, nt, 1.0, 0.5)
+    e = 1e-6
+    for idx in [tuple(x) for x in np.argwhere(g != 0)[::97][:12]]:
+        p2 = pool.copy()
+        p2[idx] += e
+        lp, _ = OF.loss_and_grad(p2, off, Ns, dirs, Rt, nt, 1.0, 0.5)
+        p2[idx] -= 2 * e
+        lm, _ = OF.loss_and_grad(p2, off, Ns, dirs, Rt, nt, 1.0, 0.5)
+        assert abs((lp - lm) / (2 * e) - g[idx]) <= 1e-5 * max(1.0, abs(g[idx]))
+
+
+def test_adam_first_step_closed_form():
+    import oracle.fit as OF
+    rng = np.random.default_rng(44)
+    g = rng.normal(size=1000)
+    p, m, v = OF.adam(np.zeros(1000), g, np.zeros(1000), np.zeros(1000), 1, 0.01, eps=1e-8)
+    # bias-corrected first moments are g and g^2: the step is -lr g / (|g| + eps)
+    assert np.allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
