@@ -9,7 +9,8 @@
  *
  * Conventions (every entry point):
  *   - All array pointers are DEVICE pointers owned by the caller, unless a comment says host.
- *     The library allocates no device memory and keeps no state between calls.
+ *     The library allocates no device memory and keeps no state between calls (the one
+ *     exception is the static workspace of shm_raycast_noalloc, described there).
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  *     The returned status covers host-side argument validation and launch errors only.
  *   - Conditions found on the device never trap: they are OR-ed into *dev_status (device
@@ -256,6 +257,28 @@ shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj
                        const shm_camera* cam, const shm_raycast_params* prm, float* rgba,
                        float* depth, float* normal, int32_t* obj_id, void* ws, size_t ws_bytes,
                        int32_t* dev_status, shm_stream stream);
+
+/* Capacity of the device-resident workspace used by shm_raycast_noalloc, in bytes. */
+#define SHM_RAYCAST_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* shm_raycast without a caller workspace.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory when they ray cast, such as a renderer embedded
+ * in a host application that owns the GPU memory budget through its own pool, or a real-time frame
+ * loop where cudaMalloc / cudaFree would synchronise the device and stall the frame.
+ *   - The workspace is a static device array of SHM_RAYCAST_NOALLOC_SCRATCH_BYTES (16 MiB) inside
+ *     libshm.so; every GPU that loads the library holds it until the process exits.  Calls whose
+ *     shm_raycast_workspace_bytes(n_obj, W, H) exceeds it return SHM_ERR_WORKSPACE and launch
+ *     nothing (512 objects at 1920x1080 fit).
+ *   - The first call on a device looks up the array's device address (with that device current)
+ *     and caches it; make that first call before any stream capture on the device.
+ *   - All calls share the one array, which keeps the previous call's contents (the counters that
+ *     must start at zero are cleared on `stream` by every call).  Calls that overlap on the GPU,
+ *     for example on two streams, race on it: serialise them.
+ *   - No device memory is allocated or freed.  Results equal shm_raycast's. */
+shm_status shm_raycast_noalloc(const shm_lut* lut, const shm_object* objs, int32_t n_obj,
+                               const shm_camera* cam, const shm_raycast_params* prm, float* rgba,
+                               float* depth, float* normal, int32_t* obj_id, int32_t* dev_status,
+                               shm_stream stream);
 
 /* ---------------------------------------------------------------- misc */
 

@@ -10,7 +10,7 @@ from .binding import (  # noqa: F401
     SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT,
     Lut, Source, ShmError, alloc_lut, like_lut, lib, lib_path,
     query, sh_basis, build_lut, build_workspace, build_workspace_bytes, pack_lut, lut_bounds, query_backward, build_lut_backward, sh_eval, fit_backward, adam_step,
-    make_camera, make_raycast_params, objects_tensor, raycast, raycast_workspace_bytes, raycast_query_count,
+    make_camera, make_raycast_params, objects_tensor, raycast, raycast_noalloc, raycast_workspace_bytes, raycast_query_count,
     records_per_glyph, record_bytes,
 )
 from .autograd import query_fn, sh_bake_fn  # noqa: F401

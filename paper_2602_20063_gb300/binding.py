@@ -79,6 +79,7 @@ _SIGS = {
     "shm_sh_eval": (C.c_int, [_I32, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_raycast_workspace_bytes": (C.c_int64, [_I32, _I32, _I32]),
     "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "shm_raycast_noalloc": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_status_string": (C.c_char_p, [C.c_int]),
     "shm_version": (C.c_int32, []),
 }
@@ -425,6 +426,23 @@ def raycast(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm: c_rayc
                            ws.numel(), _ptr(dev_status), _stream(stream))
     _check(st, "shm_raycast")
     out["_ws"] = ws
+    return out
+
+
+def raycast_noalloc(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm: c_raycast_params,
+                    want=("rgba", "depth", "normal", "obj_id"), out: dict = None, dev_status=None, stream=None) -> dict:
+    """shm_raycast_noalloc: ray casting with the library's static device workspace (no allocation)."""
+    W, H = cam.W, cam.H
+    dev = lut.data.device
+    out = {} if out is None else out
+    shapes = {"rgba": (H, W, 4), "depth": (H, W), "normal": (H, W, 3), "obj_id": (H, W)}
+    for k in want:
+        if k not in out:
+            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "obj_id" else torch.float32, device=dev)
+    st = lib().shm_raycast_noalloc(C.byref(lut.c()), _ptr(objs), n_obj, C.byref(cam), C.byref(prm),
+                                   _ptr(out.get("rgba")), _ptr(out.get("depth")), _ptr(out.get("normal")),
+                                   _ptr(out.get("obj_id")), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_raycast_noalloc")
     return out
 
 

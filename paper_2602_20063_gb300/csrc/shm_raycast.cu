@@ -14,6 +14,8 @@
 // then ranks [n_obj], ordered ids [n_obj], per-tile counts [tiles], per-tile lists [tiles][n_obj].
 #include <math.h>
 
+#include <mutex>
+
 #include "shm_internal.h"
 
 namespace shm {
@@ -314,3 +316,58 @@ cudaError_t launch_raycast(const LutView& L, const shm_object* objs, int n_obj, 
 }
 
 }  // namespace shm
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of shm_raycast (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory at the point where they ray cast: a renderer
+// running inside a host application that owns the GPU memory budget through its own pool, or a
+// real-time frame loop in which a cudaMalloc / cudaFree would synchronise the device and stall the
+// frame.  For them the workspace lives in this file-scope device array instead of a caller buffer.
+// Every GPU that loads libshm.so holds the array until the process exits.
+static __device__ __align__(256) unsigned char g_raycast_scratch[SHM_RAYCAST_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_raycast_scratch for the current device.  In host code the array's name is
+// only a host-side stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+void* raycast_scratch_address(shm_status* st)
+{
+    static std::mutex mu;
+    static void* cache[256] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        *st = SHM_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_raycast_scratch) != cudaSuccess || !p) {
+            *st = SHM_ERR_CUDA;
+            return nullptr;
+        }
+        cache[dev] = p;
+    }
+    *st = SHM_OK;
+    return cache[dev];
+}
+
+}  // namespace
+
+extern "C" shm_status shm_raycast_noalloc(const shm_lut* lut, const shm_object* objs, int32_t n_obj,
+                                          const shm_camera* cam, const shm_raycast_params* prm, float* rgba,
+                                          float* depth, float* normal, int32_t* obj_id, int32_t* dev_status,
+                                          shm_stream stream)
+{
+    if (!cam || n_obj < 0 || cam->W <= 0 || cam->H <= 0 || cam->W > 65536 || cam->H > 65536)
+        return SHM_ERR_INVALID_ARG;
+    if (shm::raycast_workspace_bytes(n_obj, cam->W, cam->H) > (int64_t)SHM_RAYCAST_NOALLOC_SCRATCH_BYTES)
+        return SHM_ERR_WORKSPACE;
+    shm_status st = SHM_OK;
+    void* ws = raycast_scratch_address(&st);
+    if (st != SHM_OK) return st;
+    return shm_raycast(lut, objs, n_obj, cam, prm, rgba, depth, normal, obj_id, ws,
+                       (size_t)SHM_RAYCAST_NOALLOC_SCRATCH_BYTES, dev_status, stream);
+}
