@@ -33,7 +33,7 @@ namespace tc {
 constexpr int TM = 128;  // table columns per tile (MMA M)
 constexpr int TN = 256;  // glyphs per tile (MMA N)
 constexpr int KC = 32;   // K per stage: 32 x 4 B = one 128-byte swizzle row
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 2;  // the producer's drain bookkeeping assumes 2 stages
 constexpr uint32_t A_BYTES = TM * KC * 4;
 constexpr uint32_t B_BYTES = TN * KC * 4;
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA producer
         uint32_t it = 0;
-        int issued[NSTAGE] = {0, 0};
+        int issued0 = 0, issued1 = 0;  // phases issued into stage 0 / 1 (NSTAGE == 2)
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             const int mt = t % num_m, nt = t / num_m;
@@ -222,17 +222,19 @@ __global__ void __launch_bounds__(256, 1)
                 tma_load_2d(smem_u32(st + A_BYTES), &mAl, c * KC, mt * TM, fb);
                 tma_load_2d(smem_u32(st + 2 * A_BYTES), &mBh, c * KC, nt * TN, fb);
                 tma_load_2d(smem_u32(st + 2 * A_BYTES + B_BYTES), &mBl, c * KC, nt * TN, fb);
-                issued[s] = (int)(it / NSTAGE) + 1;
+                if (s == 0) issued0 = (int)(it / NSTAGE) + 1; else issued1 = (int)(it / NSTAGE) + 1;
             }
         }
         if (!ok) {
             // drain: the last load issued into each stage must land before the CTA exits
-            for (int s = 0; s < NSTAGE; ++s)
-                if (issued[s] > 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                const int iss = s == 0 ? issued0 : issued1;
+                if (iss > 0) {
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)(issued[s] - 1) & 1) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
+                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)(iss - 1) & 1) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
                     }
                 }
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(256, 1)
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TN + n0, r);
                 const int g0 = nt * TN + n0;
                 if (a.direct) {
-#pragma unroll 8
+#pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int g = g0 + i;
                         if (g < a.G && col_ok) {
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(256, 1)
                     const int P = a.view.N_uniform + 2;
                     const int tex = col >> 2;
                     const int f = tex / (P * P), rem = tex % (P * P), jj = rem / P, ii = rem % P;
+#pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const float v0 = __uint_as_float(r[i]);
                         const float v1 = __shfl_down_sync(0xffffffffu, v0, 1);

@@ -54,8 +54,11 @@ def test_adam_parity(S):
     g = rng.normal(size=n).astype(np.float32)
     P, G_, M, V = (torch.from_numpy(x.copy()).cuda() for x in (p, g, m, v))
     S.adam_step(P, G_, M, V, lr=1e-2, step=7, zero_grad=True)
+    # the kernel takes float32 hyper-parameters (0.999 and 1e-2 are not float32 numbers): give the
+    # oracle the same values
+    f = lambda x: float(np.float32(x))
     pr, mr, vr = OF.adam(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64), v.astype(np.float64),
-                         7, 1e-2)
+                         7, f(1e-2), beta1=f(0.9), beta2=f(0.999), eps=f(1e-8))
     assert np.abs(P.double().cpu().numpy() - pr).max() <= 1e-6 * max(1.0, np.abs(pr).max())
     assert np.abs(M.double().cpu().numpy() - mr).max() <= 1e-6
     assert np.abs(V.double().cpu().numpy() - vr).max() <= 1e-7
