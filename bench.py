@@ -42,6 +42,21 @@ def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def reduce_over_ranks(value: float, dist, device="cpu") -> float:
+    """Max over ranks (the slowest replica sets the whole-job time); identity on one process."""
+    if dist is None or not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units of all ranks (weak scaling: each rank processes the same amount) per second of the slowest."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -860,15 +875,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_over_ranks(ms, dist, "cuda")
         dist.barrier()
     clk = clocks.stop()
     timer.active = False
     ktot = timer.totals()
     ms_step = ms / args.steps
-    value = world * work.units_per_step() / (ms_step * 1e-3)
+    value = whole_job_rate(work.units_per_step(), world, ms_step)
 
     # ---- end to end through the public API from pinned host memory
     host_out, h2d, d2h = work.e2e_setup()
@@ -884,9 +897,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_ms = a0.elapsed_time(a1) / n_e2e
     if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = reduce_over_ranks(e2e_ms, dist, "cuda")
 
     # ---- roofline of the dominant kernel
     terms = work.roofline_terms(peaks, ktot, sms)

@@ -71,7 +71,7 @@ typedef struct {
     const int32_t* N;     /* device [n_glyphs] interior resolution, N >= 1 */
     const int64_t* offset;/* device [n_glyphs] first record of each glyph */
     const float* r0;      /* device [n_glyphs] value offset, or NULL (= 0) */
-    void* data;           /* device record pool, 16-byte aligned */
+    void* data;           /* device record pool, 16-byte aligned (32-byte for SHM_LAYOUT_CELL) */
 } shm_lut;
 
 /* ---------------------------------------------------------------- sizes (host only) */

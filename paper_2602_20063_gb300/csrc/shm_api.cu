@@ -32,6 +32,8 @@ static shm_status check_lut(const shm_lut* L)
     if (L->N_uniform == 0 && (!L->N || !L->offset)) return SHM_ERR_INVALID_ARG;
     if (L->N_uniform > (1 << 20)) return SHM_ERR_INVALID_ARG;
     if (((uintptr_t)L->data & 15u) != 0) return SHM_ERR_INVALID_ARG;
+    // cell records are read with 256-bit loads: the pool must be 32-byte aligned
+    if (L->layout == SHM_LAYOUT_CELL && ((uintptr_t)L->data & 31u) != 0) return SHM_ERR_INVALID_ARG;
     return SHM_OK;
 }
 

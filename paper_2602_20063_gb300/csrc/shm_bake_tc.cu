@@ -14,8 +14,9 @@
 // leaving a relative error ~2^-21 per product, below the float32 accumulation error of K terms.
 //
 // Schedule: persistent CTAs (one per SM, 256 threads), tiles of 128 columns x 256 glyphs, K in
-// chunks of 32 (128 B rows, the swizzle atom), 2 smem stages of 96 KB, 2 TMEM accumulators of 256
-// columns (512 columns, the whole TMEM) so the epilogue of one tile overlaps the MMAs of the next.
+// chunks of 16 (64 B rows, 64-byte swizzle), 4 smem stages of 48 KB so TMA runs several chunks
+// ahead of the MMAs, 2 TMEM accumulators of 256 columns (512 columns, the whole TMEM) so the
+// epilogue of one tile overlaps the MMAs of the next.
 //   warp 0 lane 0: TMA producer        warp 1: TMEM allocation; lane 0 issues the MMAs
 //   warps 4-7: epilogue (TMEM lane quadrant = warp % 4), table writes
 // Every mbarrier wait is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, drains its own
@@ -32,8 +33,8 @@ namespace tc {
 
 constexpr int TM = 128;  // table columns per tile (MMA M)
 constexpr int TN = 256;  // glyphs per tile (MMA N)
-constexpr int KC = 32;   // K per stage: 32 x 4 B = one 128-byte swizzle row
-constexpr int NSTAGE = 2;  // the producer's drain bookkeeping assumes 2 stages
+constexpr int KC = 16;   // K per stage: 16 x 4 B = one 64-byte swizzle row
+constexpr int NSTAGE = 4;
 constexpr uint32_t A_BYTES = TM * KC * 4;
 constexpr uint32_t B_BYTES = TN * KC * 4;
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -136,15 +137,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of 1024 B (SBO).
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row atoms of 512 B (SBO).
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024u >> 4) << 32;      // stride byte offset between 8-row groups
+    d |= (uint64_t)((8u * KC * 4u) >> 4) << 32;  // stride byte offset between 8-row groups
     d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
     return d;
 }
 
@@ -206,8 +207,7 @@ __global__ void __launch_bounds__(256, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA producer
-        uint32_t it = 0;
-        int issued0 = 0, issued1 = 0;  // phases issued into stage 0 / 1 (NSTAGE == 2)
+        uint32_t it = 0;  // chunks issued so far
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
             const int mt = t % num_m, nt = t / num_m;
@@ -222,17 +222,15 @@ __global__ void __launch_bounds__(256, 1)
                 tma_load_2d(smem_u32(st + A_BYTES), &mAl, c * KC, mt * TM, fb);
                 tma_load_2d(smem_u32(st + 2 * A_BYTES), &mBh, c * KC, nt * TN, fb);
                 tma_load_2d(smem_u32(st + 2 * A_BYTES + B_BYTES), &mBl, c * KC, nt * TN, fb);
-                if (s == 0) issued0 = (int)(it / NSTAGE) + 1; else issued1 = (int)(it / NSTAGE) + 1;
             }
         }
         if (!ok) {
             // drain: the last load issued into each stage must land before the CTA exits
-            for (int s = 0; s < NSTAGE; ++s) {
-                const int iss = s == 0 ? issued0 : issued1;
-                if (iss > 0) {
-                    const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(full0 + 8 * s, (uint32_t)(iss - 1) & 1) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
-                    }
+            for (uint32_t k = 1; k <= NSTAGE && k <= it; ++k) {
+                const uint32_t last = it - k;  // the last chunk issued into stage last % NSTAGE
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(full0 + 8 * (last % NSTAGE), (last / NSTAGE) & 1) &&
+                       globaltimer() - t0 < DRAIN_LIMIT_NS) {
                 }
             }
         }
@@ -254,7 +252,7 @@ __global__ void __launch_bounds__(256, 1)
                 const uint32_t bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < KC / 8; ++kk) {
-                    const uint32_t o = kk * 32;  // 8 tf32 = 32 B along K inside the swizzle row
+                    const uint32_t o = kk * 32;  // 8 tf32 = 32 B along K inside the 64-byte swizzle row
                     mma_tf32(d, sdesc(ah + o), sdesc(bh + o), (c | kk) != 0);
                     mma_tf32(d, sdesc(ah + o), sdesc(bl + o), 1);
                     mma_tf32(d, sdesc(al + o), sdesc(bh + o), 1);
@@ -378,13 +376,14 @@ static bool make_map(CUtensorMap* m, const float* base, int rows, int Kp, int bo
     const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace tc
 
-int sh_kpad(int L) { return (((L + 1) * (L + 1) + tc::KC - 1) / tc::KC) * tc::KC; }
+// K padded to a multiple of 32 (a multiple of the stage K; the layout is part of shm_sh_basis's contract)
+int sh_kpad(int L) { return (((L + 1) * (L + 1) + 31) / 32) * 32; }
 
 int64_t sh_build_workspace_bytes(int G, int L) { return 2LL * G * sh_kpad(L) * (int64_t)sizeof(float); }
 

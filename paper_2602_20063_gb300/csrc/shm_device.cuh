@@ -154,6 +154,14 @@ __device__ __forceinline__ float4 load_rec(const void* base, int64_t rec)
     }
 }
 
+// 256-bit read-only load (sm_100+): 32 contiguous, 32-byte aligned bytes.
+__device__ __forceinline__ void ldg256(const void* p, float4& a, float4& b)
+{
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 template <int DT, int LAYOUT>
 __device__ __forceinline__ Corners fetch_corners(const void* data, const GlyphRef& G, int f, int i, int j)
 {
@@ -166,12 +174,26 @@ __device__ __forceinline__ Corners fetch_corners(const void* data, const GlyphRe
         c.c01 = load_rec<DT>(data, r + P);
         c.c11 = load_rec<DT>(data, r + P + 1);
     } else {
+        // a cell record is one aligned block (64 B f32, 32 B 16-bit): 256-bit loads
         const int64_t P = G.N + 1;
-        const int64_t r = (G.base + ((int64_t)f * P + j) * P + i) * 4;  // 4 texel records per cell
-        c.c00 = load_rec<DT>(data, r);
-        c.c10 = load_rec<DT>(data, r + 1);
-        c.c01 = load_rec<DT>(data, r + 2);
-        c.c11 = load_rec<DT>(data, r + 3);
+        const int64_t cell = G.base + ((int64_t)f * P + j) * P + i;
+        if (DT == SHM_F32) {
+            const float* p = reinterpret_cast<const float*>(data) + cell * 16;
+            ldg256(p, c.c00, c.c10);
+            ldg256(p + 8, c.c01, c.c11);
+        } else {
+            float4 lo, hi;
+            ldg256(reinterpret_cast<const uint16_t*>(data) + cell * 16, lo, hi);
+            const uint2 r0 = make_uint2(__float_as_uint(lo.x), __float_as_uint(lo.y));
+            const uint2 r1 = make_uint2(__float_as_uint(lo.z), __float_as_uint(lo.w));
+            const uint2 r2 = make_uint2(__float_as_uint(hi.x), __float_as_uint(hi.y));
+            const uint2 r3 = make_uint2(__float_as_uint(hi.z), __float_as_uint(hi.w));
+            if (DT == SHM_F16) {
+                c.c00 = h4_to_f4(r0); c.c10 = h4_to_f4(r1); c.c01 = h4_to_f4(r2); c.c11 = h4_to_f4(r3);
+            } else {
+                c.c00 = b4_to_f4(r0); c.c10 = b4_to_f4(r1); c.c01 = b4_to_f4(r2); c.c11 = b4_to_f4(r3);
+            }
+        }
     }
     return c;
 }

@@ -68,7 +68,9 @@ def test_validation_rejects_bad_arguments_without_a_device(lib):
     assert lib.shm_query(C.byref(L), 10, C.c_void_p(16), None, None, None, None, None, None, None, None, None) == 1
     L.dtype, L.data = 0, 8  # misaligned pool
     assert lib.shm_query(C.byref(L), 10, C.c_void_p(16), None, None, None, None, None, None, None, None, None) == 1
-    L.data = 16
+    L.layout, L.data = 1, 16  # cell pools need 32-byte alignment
+    assert lib.shm_query(C.byref(L), 10, C.c_void_p(16), None, None, None, None, None, None, None, None, None) == 1
+    L.layout, L.data = 0, 16
     assert lib.shm_query(C.byref(L), -1, C.c_void_p(16), None, None, None, None, None, None, None, None, None) == 1
     src = c_source()
     src.kind = 99

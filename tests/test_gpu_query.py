@@ -161,3 +161,20 @@ def test_large_N_precision(S):
     ok = ~near_edge(ref["fij"], dirs, [N], None)
     assert np.array_equal(out["fij"].cpu().numpy()[ok], ref["fij"][ok])
     check_query(out, ref)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_vector_and_scalar_io_paths_agree(S, layout):
+    """16-byte-aligned directions/outputs take 128-bit loads and stores for full warp rounds; a
+    direction view offset by one row (12 B) forces the scalar path.  Results must be identical,
+    including the ragged last round."""
+    lut, _ = _config1(11)
+    L, _ = upload_pool(S, [lut], layout=layout)
+    base = torch.from_numpy(I.directions(10001, 12)).cuda()
+    d_al = base[1:].clone()          # aligned copy
+    d_un = base[1:]                  # offset view: 12-byte shift from a 256-byte-aligned allocation
+    assert d_un.data_ptr() % 16 != 0 and d_al.data_ptr() % 16 == 0
+    a = S.query(L, d_al, want=("R", "grad", "normal", "chart", "fij"))
+    b = S.query(L, d_un, want=("R", "grad", "normal", "chart", "fij"))
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
