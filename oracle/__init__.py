@@ -325,6 +325,37 @@ def bake_sh_vjp(N, L, dlut):
     return dc
 
 
+# ----------------------------------------------------------------- mip levels (§4.7)
+def mip_samples(fine, r0=0.0):
+    """Coarse margin samples [6][Nc+4][Nc+4] (absolute radius) of one fine glyph table."""
+    fine = _c64(fine)
+    Nf = fine.shape[1] - 2
+    assert Nf % 2 == 0 and Nf >= 2
+    S = Nf // 2 + 4
+    samples = np.zeros((6, S, S))
+    lib().shmo_mip_samples(_p(fine, _d), C.c_int(Nf), C.c_double(r0), _p(samples, _d))
+    return samples
+
+
+def mip_consistent(fine, r0=0.0, r0_coarse=None):
+    """Derivative-consistent coarse level of one glyph table [6][Nf+2][Nf+2][4] (stored channel 0
+    relative to r0; the coarse one relative to r0_coarse, default r0): box-filtered fine
+    interpolant, then central-difference records."""
+    fine = _c64(fine)
+    Nc = (fine.shape[1] - 2) // 2
+    return bake_fd(Nc, mip_samples(fine, r0), r0=r0 if r0_coarse is None else r0_coarse)
+
+
+def mip_naive(fine):
+    """Naive coarse level: every record channel box-filtered over the 2x2 children."""
+    fine = _c64(fine)
+    Nf = fine.shape[1] - 2
+    Pc = Nf // 2 + 2
+    out = np.zeros((6, Pc, Pc, 4))
+    lib().shmo_mip_naive(_p(fine, _d), C.c_int(Nf), _p(out, _d))
+    return out
+
+
 # ----------------------------------------------------------------- raycast
 def make_camera(eye, fwd, right, up, fov_y_deg, W, H):
     cam = Camera()

@@ -14,6 +14,7 @@
  *   query.c       the per-direction query: direction -> face/uv -> 2x2 texels -> R, grad, normal
  *   adjoint.c     reverse-mode derivative of the query and of the SH bake (not in the paper)
  *   raycast.c     §3.1 ray / star-shaped-surface intersection with bisection + Newton
+ *   mip.c         §4.7 derivative-consistent and naive mip levels
  *
  * Storage: one glyph's table is [6][P][P][4] float64 with P = N+2, texel (i, j) of face f at
  * ((f*P + j)*P + i)*4, channels (r, r_u h, r_v h, r_uv h^2) with h = 1/N (Eq. hermite_storage).
@@ -103,6 +104,10 @@ void shmo_query_vjp_batch(const double* pool, const int64_t* off, const int32_t*
                           const double* gR, const double* gG, const double* gn,
                           double* dpool, double* ddirs);
 void shmo_bake_sh_vjp(int N, int L, const double* dlut, double* dcoeffs);
+
+/* ---------- mip.c */
+void shmo_mip_samples(const double* fine, int Nf, double r0, double* samples);
+void shmo_mip_naive(const double* fine, int Nf, double* coarse);
 
 /* ---------- raycast.c */
 typedef struct {
