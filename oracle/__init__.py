@@ -325,6 +325,55 @@ def bake_sh_vjp(N, L, dlut):
     return dc
 
 
+# ----------------------------------------------------------------- value-only baselines (§4.2, §4.5)
+RECON_NEAREST, RECON_BILINEAR, RECON_BICUBIC, RECON_FAST_BICUBIC = 0, 1, 2, 3
+
+
+def value_grid_sh(N, L, coeffs):
+    """Value table [6][N+4][N+4] of an SH function: r at every texel centre, two-texel gutter."""
+    g = np.zeros((6, N + 4, N + 4))
+    lib().shmo_value_grid_sh(C.c_int(N), C.c_int(L), _p(_c64(coeffs), _d), _p(g, _d))
+    return g
+
+
+def make_value_pool(grids):
+    """Concatenate value tables; returns (pool, offset in scalars, Ns)."""
+    Ns = np.array([g.shape[1] - 4 for g in grids], dtype=np.int32)
+    off = np.zeros(len(grids), dtype=np.int64)
+    for k in range(1, len(grids)):
+        off[k] = off[k - 1] + grids[k - 1].size
+    return np.concatenate([np.asarray(g, dtype=np.float64).reshape(-1) for g in grids]), off, Ns
+
+
+def recon(method, pool, off, Ns, dirs, glyph=None, r0=None, nthreads=None):
+    """Batched value-only reconstruction (same outputs as ``query``)."""
+    pool = _c64(pool)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    Ns = np.ascontiguousarray(Ns, dtype=np.int32)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float32)
+    Q = dirs.shape[0]
+    gl = None if glyph is None else np.ascontiguousarray(glyph, dtype=np.int32)
+    r0a = None if r0 is None else _c64(r0)
+    out = dict(R=np.zeros(Q), grad=np.zeros((Q, 3)), normal=np.zeros((Q, 3)), chart=np.zeros((Q, 2)),
+               fij=np.zeros((Q, 3), dtype=np.int32))
+    lib().shmo_recon_batch(C.c_int(method), _p(pool, _d), _p(off, _i64), _p(Ns, _i32), _p(r0a, _d), C.c_int64(Q),
+                           _p(dirs, _f), _p(gl, _i32), _p(out["R"], _d), _p(out["grad"], _d), _p(out["normal"], _d),
+                           _p(out["chart"], _d), _p(out["fij"], _i32), C.c_int(nthreads or nthreads_default()))
+    return out
+
+
+def catmull_rom(s):
+    w, dw = np.zeros(4), np.zeros(4)
+    lib().shmo_catmull_rom(C.c_double(s), _p(w, _d), _p(dw, _d))
+    return w, dw
+
+
+def bspline3(s):
+    w = np.zeros(4)
+    lib().shmo_bspline3(C.c_double(s), _p(w, _d))
+    return w
+
+
 # ----------------------------------------------------------------- mip levels (§4.7)
 def mip_samples(fine, r0=0.0):
     """Coarse margin samples [6][Nc+4][Nc+4] (absolute radius) of one fine glyph table."""

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["chart.c", "hermite.c", "sh.c", "bake.c", "procedural.c", "query.c", "adjoint.c", "raycast.c", "mip.c"]
+SOURCES = ["chart.c", "hermite.c", "sh.c", "bake.c", "procedural.c", "query.c", "adjoint.c", "raycast.c", "mip.c", "recon.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

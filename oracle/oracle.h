@@ -15,6 +15,7 @@
  *   adjoint.c     reverse-mode derivative of the query and of the SH bake (not in the paper)
  *   raycast.c     §3.1 ray / star-shaped-surface intersection with bisection + Newton
  *   mip.c         §4.7 derivative-consistent and naive mip levels
+ *   recon.c       §4.2/§4.5 value-only baselines: nearest, bilinear+FD, Catmull-Rom, B-spline
  *
  * Storage: one glyph's table is [6][P][P][4] float64 with P = N+2, texel (i, j) of face f at
  * ((f*P + j)*P + i)*4, channels (r, r_u h, r_v h, r_uv h^2) with h = 1/N (Eq. hermite_storage).
@@ -104,6 +105,16 @@ void shmo_query_vjp_batch(const double* pool, const int64_t* off, const int32_t*
                           const double* gR, const double* gG, const double* gn,
                           double* dpool, double* ddirs);
 void shmo_bake_sh_vjp(int N, int L, const double* dlut, double* dcoeffs);
+
+/* ---------- recon.c */
+enum { SHMO_RECON_NEAREST = 0, SHMO_RECON_BILINEAR = 1, SHMO_RECON_BICUBIC = 2, SHMO_RECON_FAST_BICUBIC = 3 };
+void shmo_catmull_rom(double s, double w[4], double dw[4]);
+void shmo_bspline3(double s, double w[4]);
+void shmo_recon_one(int method, const double* grid, int N, double r0, const double d[3], shmo_query_out* o);
+void shmo_recon_batch(int method, const double* pool, const int64_t* off, const int32_t* Ns, const double* r0,
+                      int64_t Q, const float* dirs, const int32_t* glyph, double* R, double* grad, double* normal,
+                      double* chart, int32_t* fij, int nthreads);
+void shmo_value_grid_sh(int N, int L, const double* coeffs, double* grid);
 
 /* ---------- mip.c */
 void shmo_mip_samples(const double* fine, int Nf, double r0, double* samples);
