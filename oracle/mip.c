@@ -16,6 +16,18 @@
 #include <stdlib.h>
 #include "oracle.h"
 
+/* Direction a + X b + Y c of fine texel (i, j) of face f with X = 2u_i - 1 = (2i - 1 - N)/N formed
+ * from the integer numerator: near cube corners two children sit exactly on a cube edge
+ * (|X| = |Y|), and the face choice there must see the exact tie (ties -> lowest axis, §3.2
+ * reading), which 2 * ((i - 1/2)/N) - 1 can break by one rounding. */
+static void child_dir(int f, int i, int j, int N, double wt[3])
+{
+    double a[3], b[3], c[3];
+    shmo_face_frame(f, a, b, c);
+    const double X = (double)(2 * i - 1 - N) / (double)N, Y = (double)(2 * j - 1 - N) / (double)N;
+    for (int q = 0; q < 3; ++q) wt[q] = a[q] + X * b[q] + Y * c[q];
+}
+
 void shmo_mip_samples(const double* fine, int Nf, double r0, double* samples)
 {
     int Nc = Nf / 2, S = Nc + 4;
@@ -28,7 +40,7 @@ void shmo_mip_samples(const double* fine, int Nf, double r0, double* samples)
                     for (int a = 0; a < 2; ++a) {
                         int i_f = 2 * ic - 1 + a, j_f = 2 * jc - 1 + b;
                         double wt[3];
-                        shmo_dir_tilde(f, shmo_texel_centre(i_f, Nf), shmo_texel_centre(j_f, Nf), wt);
+                        child_dir(f, i_f, j_f, Nf, wt);
                         shmo_query_out o;
                         shmo_query_one(fine, Nf, r0, wt, &o);
                         acc += o.R;

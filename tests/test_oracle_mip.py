@@ -97,3 +97,35 @@ def test_lod_table_trend(oracle):
     assert ratios[0] > ratios[1] > ratios[2] > 1.0
     assert ratios[2] < 2.0
     assert means[0] < means[1] < means[2]
+
+
+def test_children_on_cube_edges_take_the_exact_tie(oracle):
+    """Table = face index on each face (derivatives 0): every coarse sample is the mean face index of
+    its four children.  Children near cube corners lie exactly on a cube edge (|X| = |Y| > 1); the
+    expected face comes from exact rational arithmetic with ties -> lowest axis (§3.2 reading)."""
+    from fractions import Fraction
+    Nf = 6
+    P = Nf + 2
+    lut = np.zeros((6, P, P, 4))
+    for f in range(6):
+        lut[f, ..., 0] = f
+    samples = oracle.mip_samples(lut)
+    Sg = Nf // 2 + 4
+    ties = 0
+    for f in range(6):
+        k, sg = f // 2, (-1 if f % 2 else 1)
+        for jj in range(Sg):
+            for ii in range(Sg):
+                faces = []
+                for b in range(2):
+                    for a in range(2):
+                        X = Fraction(2 * (2 * ii - 3 + a) - 1 - Nf, Nf)
+                        Y = Fraction(2 * (2 * jj - 3 + b) - 1 - Nf, Nf)
+                        d = [Fraction(0)] * 3
+                        d[k], d[(k + 1) % 3], d[(k + 2) % 3] = Fraction(sg), X, Y
+                        m = max(abs(x) for x in d)
+                        kk = min(q for q in range(3) if abs(d[q]) == m)
+                        ties += sum(abs(x) == m for x in d) > 1
+                        faces.append(2 * kk + (d[kk] < 0))
+                assert abs(samples[f, jj, ii] - sum(faces) / 4.0) < 1e-12, (f, jj, ii, faces)
+    assert ties > 0
