@@ -57,7 +57,12 @@ typedef enum { SHM_F32 = 0, SHM_F16 = 1, SHM_BF16 = 2 } shm_dtype;
  *                     cell record holds its 2x2 corner texels (i,j),(i+1,j),(i,j+1),(i+1,j+1)
  *                     back to back (64 B f32, 32 B 16-bit), so a query reads one aligned
  *                     64 B / 32 B block.  Same values, 4x the bytes of the texel layout. */
-typedef enum { SHM_LAYOUT_TEXEL = 0, SHM_LAYOUT_CELL = 1 } shm_layout;
+/*   SHM_LAYOUT_VALUE: a value-only table for the reconstruction baselines of shm_query_recon
+ *                     (§4.2, §4.5): one scalar per texel (4 B f32, 2 B 16-bit), [6][N+4][N+4]
+ *                     per glyph with a two-texel gutter, entry (ii, jj) = texel (ii-1, jj-1),
+ *                     i = -1 .. N+2, each evaluated at its own centre in the face's chart (a
+ *                     4 x 4 footprint needs texels i-1 .. i+2).  Not accepted by shm_query. */
+typedef enum { SHM_LAYOUT_TEXEL = 0, SHM_LAYOUT_CELL = 1, SHM_LAYOUT_VALUE = 2 } shm_layout;
 
 /* A pool of per-glyph tables.  Represented radius = r0[g] + stored channel 0.
  * If N_uniform > 0 every glyph has interior resolution N_uniform and glyph g starts at record
@@ -76,10 +81,11 @@ typedef struct {
 
 /* ---------------------------------------------------------------- sizes (host only) */
 
-/* Records one glyph of resolution N occupies in `layout`: 6(N+2)^2 or 6(N+1)^2. */
+/* Records one glyph of resolution N occupies in `layout`: 6(N+2)^2, 6(N+1)^2 or 6(N+4)^2. */
 int64_t shm_records_per_glyph(int32_t N, int32_t layout);
 
-/* Bytes of one record: 4 channels x 4 B (f32) or 2 B (16-bit), x 4 for the cell layout. */
+/* Bytes of one record: 4 channels x 4 B (f32) or 2 B (16-bit), x 4 for the cell layout, one
+ * channel for the value layout. */
 int64_t shm_record_bytes(int32_t dtype, int32_t layout);
 
 /* Host: fills offset_host[G] (records) for the per-glyph resolutions N_host[G] and returns
@@ -105,6 +111,31 @@ shm_status shm_lut_layout(int32_t G, const int32_t* N_host, int32_t dtype, int32
 shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
                      const int64_t* seg, float* R, float* grad, float* normal, float* chart,
                      int32_t* fij, int32_t* dev_status, shm_stream stream);
+
+/* Value-only reconstruction baselines (§4.2 Table psnr_value, §4.5 Table cost_extended) on a
+ * SHM_LAYOUT_VALUE table, with the chart, glyph selection, outputs and status rules of shm_query.
+ * With x = uN + 1/2 (texel i at x = i) and (i, s) the cell of x as in shm_query:
+ *   SHM_RECON_NEAREST       value of the interior texel whose square holds (u, v); R_u = R_v = 0
+ *   SHM_RECON_BILINEAR      bilinear value; R_u, R_v by central differences of the bilinear value
+ *                           one texel to either side (u +- h, v +- h), 5 bilinear lookups in all
+ *   SHM_RECON_BICUBIC       16-tap Catmull-Rom (interpolating) value and its analytic gradient
+ *   SHM_RECON_FAST_BICUBIC  cubic B-spline, the filter of the 4-bilinear-fetch "fast bicubic"
+ *                           (GPU Gems 2 ch. 20), evaluated from its 16 taps; R_u, R_v by central
+ *                           differences of the B-spline value at u +- h, v +- h
+ * Cell indices of the shifted lookups are clamped to [-1, N+1] (2-tap) or [0, N] (4-tap), the
+ * local coordinate then extending the nearest cell's polynomial.  The gradient and normal then
+ * follow §3.4 exactly as in shm_query.  SHM_ERR_INVALID_ARG for a table that is not
+ * SHM_LAYOUT_VALUE or an unknown method. */
+typedef enum {
+    SHM_RECON_NEAREST = 0,
+    SHM_RECON_BILINEAR = 1,
+    SHM_RECON_BICUBIC = 2,
+    SHM_RECON_FAST_BICUBIC = 3
+} shm_recon;
+
+shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const float* dirs,
+                           const int32_t* glyph, const int64_t* seg, float* R, float* grad, float* normal,
+                           float* chart, int32_t* fij, int32_t* dev_status, shm_stream stream);
 
 /* ---------------------------------------------------------------- bake (Algorithm 1) */
 
@@ -162,6 +193,9 @@ int64_t shm_build_workspace_bytes(const shm_lut* lut, const shm_source* src);
 
 /* Writes every record of every glyph of `lut` (any dtype/layout) from `src` (Algorithm 1:
  * gutter texels evaluated at their own centres, derivative channels in each face's chart).
+ * A SHM_LAYOUT_VALUE table receives the value at every texel centre of its two-texel gutter
+ * grid: SH sources by direct evaluation (float32 CUDA cores; ws ignored), sampled sources copy
+ * their margin grid, which is that same grid.
  * SH sources: with ws != NULL and ws_bytes >= shm_build_workspace_bytes the contraction runs on
  * the tensor cores (tcgen05, 3xTF32 split, float32-grade accuracy); with ws == NULL on the
  * float32 CUDA cores.  A non-NULL ws smaller than required returns SHM_ERR_WORKSPACE. */
@@ -176,6 +210,18 @@ shm_status shm_pack_lut(const shm_lut* src, const shm_lut* dst, shm_stream strea
  * max|r0 + r| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16 over the glyph's texels.
  * rmax: device float32 [n_glyphs]. */
 shm_status shm_lut_bounds(const shm_lut* lut, float* rmax, shm_stream stream);
+
+/* Derivative-consistent mip level (§4.7, Table lod): writes every record of `coarse` from
+ * `fine`, glyph by glyph, with coarse N = fine N / 2 (fine N even).  The coarse value sample of
+ * coarse texel (i, j) -- gutter ring and one-texel bake margin included -- is the mean of the fine
+ * interpolant (shm_query's R) at the centres of fine texels 2i-1, 2i by 2j-1, 2j (directions
+ * outside the face are served by the neighbouring face); the derivative channels follow by central
+ * differences of those samples, as the finite-difference bake of shm_build_lut.  Any dtype/layout
+ * on either side; 16-bit stores round to nearest even; coarse channel 0 is relative to the coarse
+ * r0.  The tables must not overlap.  Uniform resolutions are checked here (SHM_ERR_INVALID_ARG);
+ * with per-glyph arrays a glyph whose resolutions do not pair gets NaN records and SHM_DEV_BOUNDS
+ * in *dev_status (device int32, may be NULL). */
+shm_status shm_build_mip(const shm_lut* fine, const shm_lut* coarse, int32_t* dev_status, shm_stream stream);
 
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 

@@ -17,14 +17,15 @@ import torch
 from . import build as _build
 
 SHM_F32, SHM_F16, SHM_BF16 = 0, 1, 2
-SHM_LAYOUT_TEXEL, SHM_LAYOUT_CELL = 0, 1
+SHM_LAYOUT_TEXEL, SHM_LAYOUT_CELL, SHM_LAYOUT_VALUE = 0, 1, 2
+SHM_RECON_NEAREST, SHM_RECON_BILINEAR, SHM_RECON_BICUBIC, SHM_RECON_FAST_BICUBIC = 0, 1, 2, 3
 SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM = 0, 1, 2, 3
 SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT = 1, 2, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error", 5: "timeout"}
 
 DTYPES = {SHM_F32: torch.float32, SHM_F16: torch.float16, SHM_BF16: torch.bfloat16}
 DTYPE_NAMES = {"f32": SHM_F32, "f16": SHM_F16, "bf16": SHM_BF16}
-LAYOUT_NAMES = {"texel": SHM_LAYOUT_TEXEL, "cell": SHM_LAYOUT_CELL}
+LAYOUT_NAMES = {"texel": SHM_LAYOUT_TEXEL, "cell": SHM_LAYOUT_CELL, "value": SHM_LAYOUT_VALUE}
 
 
 class ShmError(RuntimeError):
@@ -66,12 +67,14 @@ _SIGS = {
     "shm_record_bytes": (C.c_int64, [_I32, _I32]),
     "shm_lut_layout": (C.c_int, [_I32, _VP, _I32, _I32, _VP, _VP]),
     "shm_query": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_query_recon": (C.c_int, [_VP, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_sh_basis_bytes": (C.c_int64, [_I32, _I32]),
     "shm_sh_basis": (C.c_int, [_I32, _I32, _VP, _VP]),
     "shm_build_lut": (C.c_int, [_VP, _VP, _VP, _SZ, _VP]),
     "shm_build_workspace_bytes": (C.c_int64, [_VP, _VP]),
     "shm_pack_lut": (C.c_int, [_VP, _VP, _VP]),
     "shm_lut_bounds": (C.c_int, [_VP, _VP, _VP]),
+    "shm_build_mip": (C.c_int, [_VP, _VP, _VP, _VP]),
     "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
     "shm_fit_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
@@ -145,7 +148,7 @@ def record_bytes(dtype: int, layout: int) -> int:
 
 
 def records_per_glyph_host(N: int, layout: int) -> int:
-    P = N + 1 if layout == SHM_LAYOUT_CELL else N + 2
+    P = N + 1 if layout == SHM_LAYOUT_CELL else (N + 4 if layout == SHM_LAYOUT_VALUE else N + 2)
     return 6 * P * P
 
 
@@ -182,6 +185,8 @@ def alloc_lut(n_glyphs: int, N, dtype: int = SHM_F32, layout: int = SHM_LAYOUT_T
     rb = 16 if dtype == SHM_F32 else 8
     if layout == SHM_LAYOUT_CELL:
         rb *= 4
+    elif layout == SHM_LAYOUT_VALUE:
+        rb //= 4
     elem = 4 if dtype == SHM_F32 else 2
     if isinstance(N, int):
         Ns = None
@@ -216,7 +221,7 @@ def like_lut(L: Lut, dtype: int = None, layout: int = None, r0="same", zero=Fals
         N = L.N_uniform
     else:
         N = [int(n) for n in L.N.tolist()]
-    rr = (L.r0 if r0 == "same" else r0)
+    rr = (L.r0 if isinstance(r0, str) else r0)
     out = alloc_lut(L.n_glyphs, N, dtype, layout, r0=None, device=L.data.device, zero=zero)
     if rr is not None:
         out.r0 = torch.as_tensor(rr, dtype=torch.float32, device=L.data.device).reshape(-1).contiguous()
@@ -245,6 +250,26 @@ def query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.T
 
 
 # ------------------------------------------------------------------------------------------- bake
+def query_recon(lut: Lut, method: int, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.Tensor = None,
+                want=("R", "grad", "normal"), out: dict = None, dev_status: torch.Tensor = None, stream=None) -> dict:
+    """shm_query_recon: value-only reconstruction baseline `method` on a SHM_LAYOUT_VALUE table."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    _need(glyph, torch.int32, (Q,), "glyph")
+    _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
+    dev = dirs.device
+    out = {} if out is None else out
+    shapes = {"R": (Q,), "grad": (Q, 3), "normal": (Q, 3), "chart": (Q, 2), "fij": (Q, 3)}
+    for k in want:
+        if k not in out:
+            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "fij" else torch.float32, device=dev)
+    st = lib().shm_query_recon(C.byref(lut.c()), int(method), Q, _ptr(dirs), _ptr(glyph), _ptr(seg),
+                               _ptr(out.get("R")), _ptr(out.get("grad")), _ptr(out.get("normal")),
+                               _ptr(out.get("chart")), _ptr(out.get("fij")), _ptr(dev_status), _stream(stream))
+    _check(st, "shm_query_recon")
+    return out
+
+
 def sh_basis(N: int, L: int, device="cuda", stream=None) -> torch.Tensor:
     nbytes = int(lib().shm_sh_basis_bytes(N, L))
     if nbytes < 0:
@@ -309,6 +334,37 @@ def lut_bounds(lut: Lut, stream=None) -> torch.Tensor:
     r = torch.empty(lut.n_glyphs, dtype=torch.float32, device=lut.data.device)
     _check(lib().shm_lut_bounds(C.byref(lut.c()), _ptr(r), _stream(stream)), "shm_lut_bounds")
     return r
+
+
+def mip_like(fine: Lut, dtype: int = None, layout: int = None, r0="same", zero=False) -> Lut:
+    """A table for the next mip level of `fine`: every glyph at half the resolution."""
+    if fine.N_uniform > 0:
+        N = fine.N_uniform // 2
+    else:
+        N = [int(n) // 2 for n in fine.N.tolist()]
+    dtype = fine.dtype if dtype is None else dtype
+    layout = fine.layout if layout is None else layout
+    out = alloc_lut(fine.n_glyphs, N, dtype, layout, device=fine.data.device, zero=zero)
+    rr = fine.r0 if isinstance(r0, str) else r0
+    if rr is not None:
+        out.r0 = torch.as_tensor(rr, dtype=torch.float32, device=fine.data.device).reshape(-1).contiguous()
+    return out
+
+
+def build_mip(fine: Lut, coarse: Lut, dev_status: torch.Tensor = None, stream=None) -> Lut:
+    """shm_build_mip: derivative-consistent coarse level (coarse N = fine N / 2) written into coarse."""
+    _need(dev_status, torch.int32, name="dev_status")
+    _check(lib().shm_build_mip(C.byref(fine.c()), C.byref(coarse.c()), _ptr(dev_status), _stream(stream)),
+           "shm_build_mip")
+    return coarse
+
+
+def mip_chain(fine: Lut, levels: int, dtype: int = None, layout: int = None, stream=None) -> list:
+    """[fine, level 1, ..., level `levels`], each built from the previous one on the device."""
+    chain = [fine]
+    for _ in range(levels):
+        chain.append(build_mip(chain[-1], mip_like(chain[-1], dtype, layout), stream=stream))
+    return chain
 
 
 # ------------------------------------------------------------------------------------------- adjoint

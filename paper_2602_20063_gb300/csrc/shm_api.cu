@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <vector>
 
 #include "shm_internal.h"
 
@@ -22,7 +23,8 @@ int sm_count()
 }
 
 static bool valid_dtype(int d) { return d == SHM_F32 || d == SHM_F16 || d == SHM_BF16; }
-static bool valid_layout(int l) { return l == SHM_LAYOUT_TEXEL || l == SHM_LAYOUT_CELL; }
+static bool valid_layout(int l) { return l == SHM_LAYOUT_TEXEL || l == SHM_LAYOUT_CELL || l == SHM_LAYOUT_VALUE; }
+static bool hermite_layout(int l) { return l == SHM_LAYOUT_TEXEL || l == SHM_LAYOUT_CELL; }
 
 static shm_status check_lut(const shm_lut* L)
 {
@@ -53,28 +55,27 @@ static LutView view(const shm_lut* L)
 
 static shm_status map_cuda(cudaError_t e) { return e == cudaSuccess ? SHM_OK : SHM_ERR_CUDA; }
 
-// Largest per-glyph N: uniform N, or read from the device array (one small synchronous copy
-// on `stream`; callers with N_uniform avoid it).
-static int max_N_of(const shm_lut* L, cudaStream_t s, shm_status* st)
+// Glyph resolutions for the launch grids: uniform N, or the per-glyph array read from the device
+// (one synchronous copy on `stream`; callers with N_uniform avoid it).
+static Sizes sizes_of(const shm_lut* L, cudaStream_t s, shm_status* st, std::vector<int32_t>& buf)
 {
     *st = SHM_OK;
-    if (L->N_uniform > 0) return L->N_uniform;
-    int mx = 0;
-    const int G = L->n_glyphs;
-    int32_t buf[1024];
-    for (int g0 = 0; g0 < G; g0 += 1024) {
-        const int n = G - g0 < 1024 ? G - g0 : 1024;
-        if (cudaMemcpyAsync(buf, L->N + g0, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            *st = SHM_ERR_CUDA;
-            return 0;
-        }
-        for (int q = 0; q < n; ++q) {
-            if (buf[q] < 1 || buf[q] > (1 << 20)) { *st = SHM_ERR_INVALID_ARG; return 0; }
-            if (buf[q] > mx) mx = buf[q];
-        }
+    Sizes z{L->n_glyphs, L->N_uniform, nullptr, L->N_uniform};
+    if (L->N_uniform > 0) return z;
+    buf.resize((size_t)L->n_glyphs);
+    if (cudaMemcpyAsync(buf.data(), L->N, sizeof(int32_t) * buf.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        *st = SHM_ERR_CUDA;
+        return z;
     }
-    return mx;
+    int mx = 0;
+    for (int32_t n : buf) {
+        if (n < 1 || n > (1 << 20)) { *st = SHM_ERR_INVALID_ARG; return z; }
+        if (n > mx) mx = n;
+    }
+    z.N_host = buf.data();
+    z.max_N = mx;
+    return z;
 }
 
 }  // namespace shm
@@ -93,6 +94,7 @@ int64_t shm_record_bytes(int32_t dtype, int32_t layout)
 {
     if (!valid_dtype(dtype) || !valid_layout(layout)) return -1;
     const int64_t b = (dtype == SHM_F32) ? 16 : 8;
+    if (layout == SHM_LAYOUT_VALUE) return b / 4;
     return layout == SHM_LAYOUT_CELL ? 4 * b : b;
 }
 
@@ -116,6 +118,7 @@ shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     if (Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
     QueryArgs a;
     a.L = view(lut);
@@ -130,6 +133,30 @@ shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int
     a.fij = fij;
     a.dev_status = dev_status;
     return map_cuda(launch_query_fwd(a, (cudaStream_t)stream));
+}
+
+shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const float* dirs, const int32_t* glyph,
+                           const int64_t* seg, float* R, float* grad, float* normal, float* chart, int32_t* fij,
+                           int32_t* dev_status, shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (lut->layout != SHM_LAYOUT_VALUE) return SHM_ERR_INVALID_ARG;
+    if (method < SHM_RECON_NEAREST || method > SHM_RECON_FAST_BICUBIC) return SHM_ERR_INVALID_ARG;
+    if (Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
+    QueryArgs a;
+    a.L = view(lut);
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = glyph;
+    a.seg = glyph ? nullptr : seg;
+    a.R = R;
+    a.grad = grad;
+    a.normal = normal;
+    a.chart = chart;
+    a.fij = fij;
+    a.dev_status = dev_status;
+    return map_cuda(launch_query_recon(a, method, (cudaStream_t)stream));
 }
 
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
@@ -165,6 +192,10 @@ shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, si
     switch (src->kind) {
     case SHM_SRC_SH:
         if (lut->N_uniform <= 0) return SHM_ERR_UNSUPPORTED;
+        if (lut->layout == SHM_LAYOUT_VALUE) {
+            if (src->L < 0 || src->L > 20 || !src->coeffs) return SHM_ERR_INVALID_ARG;
+            return map_cuda(launch_sh_value(v, lut->data, src->L, src->coeffs, s));
+        }
         if (src->L < 0 || src->L > 20 || !src->coeffs || !src->basis) return SHM_ERR_INVALID_ARG;
         if (ws) {
             if ((int64_t)ws_bytes < sh_build_workspace_bytes(lut->n_glyphs, src->L) || ((uintptr_t)ws & 15u))
@@ -180,9 +211,10 @@ shm_status shm_build_lut(const shm_lut* lut, const shm_source* src, void* ws, si
             return SHM_ERR_INVALID_ARG;
         if (src->kind == SHM_SRC_FBM && (src->octaves < 0 || src->octaves > 32 || (src->octaves > 0 && !src->keys)))
             return SHM_ERR_INVALID_ARG;
-        const int mx = max_N_of(lut, s, &st);
+        std::vector<int32_t> buf;
+        const Sizes z = sizes_of(lut, s, &st, buf);
         if (st != SHM_OK) return st;
-        return map_cuda(launch_fd_build(v, lut->data, *src, mx, s));
+        return map_cuda(launch_fd_build(v, lut->data, *src, z, s));
     }
     default:
         return SHM_ERR_INVALID_ARG;
@@ -193,26 +225,50 @@ shm_status shm_pack_lut(const shm_lut* src, const shm_lut* dst, shm_stream strea
 {
     shm_status st = check_lut(src);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(src->layout) || !hermite_layout(dst->layout)) return SHM_ERR_UNSUPPORTED;
     st = check_lut(dst);
     if (st != SHM_OK) return st;
     if (src->n_glyphs != dst->n_glyphs) return SHM_ERR_INVALID_ARG;
     if ((src->N_uniform > 0) != (dst->N_uniform > 0)) return SHM_ERR_INVALID_ARG;
     if (src->N_uniform > 0 && src->N_uniform != dst->N_uniform) return SHM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int mx = max_N_of(dst, s, &st);
+    std::vector<int32_t> buf;
+    const Sizes z = sizes_of(dst, s, &st, buf);
     if (st != SHM_OK) return st;
-    return map_cuda(launch_pack(view(src), view(dst), dst->data, mx, s));
+    return map_cuda(launch_pack(view(src), view(dst), dst->data, z, s));
 }
 
 shm_status shm_lut_bounds(const shm_lut* lut, float* rmax, shm_stream stream)
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     if (!rmax) return SHM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int mx = max_N_of(lut, s, &st);
+    std::vector<int32_t> buf;
+    const Sizes z = sizes_of(lut, s, &st, buf);
     if (st != SHM_OK) return st;
-    return map_cuda(launch_bounds(view(lut), rmax, mx, s));
+    return map_cuda(launch_bounds(view(lut), rmax, z, s));
+}
+
+shm_status shm_build_mip(const shm_lut* fine, const shm_lut* coarse, int32_t* dev_status, shm_stream stream)
+{
+    shm_status st = check_lut(fine);
+    if (st != SHM_OK) return st;
+    if (!hermite_layout(fine->layout)) return SHM_ERR_UNSUPPORTED;
+    st = check_lut(coarse);
+    if (st != SHM_OK) return st;
+    if (!hermite_layout(coarse->layout)) return SHM_ERR_UNSUPPORTED;
+    if (fine->n_glyphs != coarse->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if ((fine->N_uniform > 0) != (coarse->N_uniform > 0)) return SHM_ERR_INVALID_ARG;
+    if (fine->N_uniform > 0 && (fine->N_uniform % 2 != 0 || coarse->N_uniform * 2 != fine->N_uniform))
+        return SHM_ERR_INVALID_ARG;
+    if (fine->data == coarse->data) return SHM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> buf;
+    const Sizes z = sizes_of(coarse, s, &st, buf);
+    if (st != SHM_OK) return st;
+    return map_cuda(launch_mip(view(fine), view(coarse), coarse->data, dev_status, z, s));
 }
 
 shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
@@ -221,6 +277,7 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, 
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     st = check_lut(dlut);
     if (st != SHM_OK) return st;
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
@@ -252,6 +309,7 @@ shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, co
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     st = check_lut(dlut);
     if (st != SHM_OK) return st;
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
@@ -319,6 +377,7 @@ shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     if (!cam || !prm || n_obj < 0 || (n_obj > 0 && !objs)) return SHM_ERR_INVALID_ARG;
     if (cam->W <= 0 || cam->H <= 0 || cam->W > 65536 || cam->H > 65536) return SHM_ERR_INVALID_ARG;
     if (prm->march < 1 || prm->march > 4096 || prm->bisect < 0 || prm->bisect > 64 || prm->newton < 0 ||

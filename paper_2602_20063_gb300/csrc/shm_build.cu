@@ -383,16 +383,21 @@ __device__ float fbm(const Vec3& w, const shm_source& src)
 // FD bake: 16x16 texel tile per CTA, 18x18 samples (one-texel halo) in shared memory.
 constexpr int FT = 16, FS = FT + 2, MAX_BUMPS_SMEM = 128;
 
-__global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_source src, int g_base)
+// VALUE: the table is a SHM_LAYOUT_VALUE grid, which is the margin sample grid itself: tiles then
+// cover the (N+4)^2 samples directly and store them (plus the value offset), no differences.
+template <class Map, bool VALUE>
+__global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
 {
     __shared__ float Sm[FS][FS];
     __shared__ float bump[MAX_BUMPS_SMEM][5];
-    const int g = g_base + blockIdx.z, f = blockIdx.y;
+    int tile;
+    const int g = map_block(map, tile), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
     const int N = Gr.N, P = N + 2, S = N + 4;
-    const int tiles = (P + FT - 1) / FT;
-    if ((int)blockIdx.x >= tiles * tiles) return;
-    const int i0 = (blockIdx.x % tiles) * FT, j0 = (blockIdx.x / tiles) * FT;
+    const int step = VALUE ? FS : FT;
+    const int tiles = ((VALUE ? S : P) + step - 1) / step;
+    if (tile >= tiles * tiles) return;
+    const int i0 = (tile % tiles) * step, j0 = (tile / tiles) * step;
     const int tid = threadIdx.x;
     const int k = f >> 1;
     const float sg = (f & 1) ? -1.0f : 1.0f;
@@ -446,6 +451,15 @@ __global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_s
             }
         }
     }
+    if constexpr (VALUE) {
+        for (int r = 0; r < 2; ++r) {
+            if (!live[r]) continue;
+            const int e = tid + r * 256;
+            const int ii = i0 + (e % FS), jj = j0 + (e / FS);
+            store_val(data, out.dtype, Gr.base + ((int64_t)f * S + jj) * S + ii, acc[r] + base);
+        }
+        return;
+    }
     for (int r = 0; r < 2; ++r) {
         const int e = tid + r * 256;
         if (e < FS * FS) Sm[e / FS][e % FS] = acc[r];
@@ -463,25 +477,93 @@ __global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_s
     store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
 }
 
-cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, int max_N, cudaStream_t s)
+static int64_t fd_tiles(int N)
 {
-    const int tiles = (max_N + 2 + FT - 1) / FT;
-    for (int g0 = 0; g0 < out.n_glyphs; g0 += 65535) {
-        const int n = min(65535, out.n_glyphs - g0);
-        k_fd_build<<<dim3(tiles * tiles, 6, n), 256, 0, s>>>(out, data, src, g0);
+    const int64_t t = (N + 2 + FT - 1) / FT;
+    return t * t;
+}
+
+static int64_t value_tiles(int N)
+{
+    const int64_t t = (N + 4 + FS - 1) / FS;
+    return t * t;
+}
+
+cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, const Sizes& sz, cudaStream_t s)
+{
+    if (out.layout == SHM_LAYOUT_VALUE)
+        return for_each_glyph_chunk(sz, value_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
+            k_fd_build<std::decay_t<decltype(map)>, true><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
+        });
+    return for_each_glyph_chunk(sz, fd_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
+        k_fd_build<std::decay_t<decltype(map)>, false><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
+    });
+}
+
+// ------------------------------------------------------------------------------------------
+// Value table of SH glyphs (SHM_LAYOUT_VALUE): r at every texel centre of the two-texel-gutter
+// grid.  One thread per grid entry: the K basis values of its direction are formed once and
+// applied to SH_VALUE_GLYPHS glyphs (blockIdx.y picks the glyph group).
+constexpr int SH_VALUE_GLYPHS = 32;
+
+__global__ void __launch_bounds__(128) k_sh_value(LutView out, void* data, int L, const float* __restrict__ coeffs)
+{
+    const int N = out.N_uniform, S = N + 4;
+    const int64_t T = 6LL * S * S;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= T) return;
+    const int f = (int)(e / ((int64_t)S * S)), rem = (int)(e % ((int64_t)S * S)), jj = rem / S, ii = rem % S;
+    // texel (ii-1, jj-1): 2u - 1 = (2(ii-1) - 1 - N)/N
+    const float X = (float)(2 * ii - 3 - N) / (float)N, Y = (float)(2 * jj - 3 - N) / (float)N;
+    const TexelFrame fr = texel_frame(f, X, Y);
+    const int K = (L + 1) * (L + 1);
+    float Tl[(SH_LMAX + 1) * (SH_LMAX + 2) / 2];
+    float C[SH_LMAX + 1], Sn[SH_LMAX + 1];
+    legendre_table(L, fr.w.z, Tl);
+    cs_table(L, fr.w.x, fr.w.y, C, Sn);
+    const int g0 = blockIdx.y * SH_VALUE_GLYPHS, g1 = min(out.n_glyphs, g0 + SH_VALUE_GLYPHS);
+    float acc[SH_VALUE_GLYPHS];
+#pragma unroll
+    for (int q = 0; q < SH_VALUE_GLYPHS; ++q) acc[q] = 0.0f;
+    for (int l = 0; l <= L; ++l)
+        for (int mm = -l; mm <= l; ++mm) {
+            const int m = mm < 0 ? -mm : mm;
+            const float y = ylm_derivs(Tl, l, m, mm < 0, C, Sn).v;
+            const int k = l * l + l + mm;
+#pragma unroll
+            for (int q = 0; q < SH_VALUE_GLYPHS; ++q)
+                if (g0 + q < g1) acc[q] = fmaf(__ldg(coeffs + (int64_t)(g0 + q) * K + k), y, acc[q]);
+        }
+    for (int q = 0; q < SH_VALUE_GLYPHS && g0 + q < g1; ++q) {
+        const GlyphRef G = glyph_ref(out, g0 + q);
+        store_val(data, out.dtype, G.base + e, acc[q] - G.r0);
     }
+}
+
+cudaError_t launch_sh_value(const LutView& out, void* data, int L, const float* coeffs, cudaStream_t s)
+{
+    const int S = out.N_uniform + 4;
+    const int64_t T = 6LL * S * S;
+    const unsigned gy = (unsigned)((out.n_glyphs + SH_VALUE_GLYPHS - 1) / SH_VALUE_GLYPHS);
+    if (gy > 65535u) return cudaErrorInvalidConfiguration;
+    k_sh_value<<<dim3((unsigned)((T + 127) / 128), gy), 128, 0, s>>>(out, data, L, coeffs);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------
 // Pack: one thread per destination record.
-__global__ void __launch_bounds__(256) k_pack(LutView src, LutView dst, void* ddata, int g_base)
+constexpr int PACK_PER_BLOCK = 1024;
+
+template <class Map>
+__global__ void __launch_bounds__(256) k_pack(LutView src, LutView dst, void* ddata, const __grid_constant__ Map map)
 {
-    const int g = g_base + blockIdx.y;
+    int blk;
+    const int g = map_block(map, blk);
     const GlyphRef Gs = glyph_ref(src, g), Gd = glyph_ref(dst, g);
     const int N = Gd.N;
     const int64_t nrec = records_per_glyph(N, dst.layout);
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r_end = min(nrec, (int64_t)(blk + 1) * PACK_PER_BLOCK);
+    for (int64_t r = (int64_t)blk * PACK_PER_BLOCK + threadIdx.x; r < r_end; r += blockDim.x) {
         const float dr0 = Gs.r0 - Gd.r0;
         if (dst.layout == SHM_LAYOUT_TEXEL) {
             const int P = N + 2;
@@ -501,27 +583,32 @@ __global__ void __launch_bounds__(256) k_pack(LutView src, LutView dst, void* dd
     }
 }
 
-cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, int max_N, cudaStream_t s)
+cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, const Sizes& sz, cudaStream_t s)
 {
-    const int64_t maxrec = records_per_glyph(max_N, dst.layout);
-    int64_t bx = (maxrec + 255) / 256;
-    if (bx > 65535) bx = 65535;
-    for (int g0 = 0; g0 < dst.n_glyphs; g0 += 65535)
-        k_pack<<<dim3((unsigned)bx, min(65535, dst.n_glyphs - g0)), 256, 0, s>>>(src, dst, dst_data, g0);
-    return cudaGetLastError();
+    const int layout = dst.layout;
+    auto blocks = [layout](int N) { return (records_per_glyph(N, layout) + PACK_PER_BLOCK - 1) / PACK_PER_BLOCK; };
+    return for_each_glyph_chunk(sz, blocks, [&](unsigned bx, unsigned bz, const auto& map) {
+        k_pack<<<dim3(bx, 1, bz), 256, 0, s>>>(src, dst, dst_data, map);
+    });
 }
 
 // ------------------------------------------------------------------------------------------
 // Bounds: per cell, |r| <= max|r0 + r_ab| + (max|r_u h| + max|r_v h|)/4 + max|r_uv h^2|/16 over the
 // cell's four corners (value weights are >= 0 and sum to 1; sum_a |H^d_a| = s(1-s) <= 1/4).
-__global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, int g_base)
+constexpr int BOUNDS_PER_BLOCK = 2048;
+
+template <class Map>
+__global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, const __grid_constant__ Map map)
 {
-    const int g = g_base + blockIdx.y;
+    __shared__ float warp_best[8];
+    int blk;
+    const int g = map_block(map, blk);
     const GlyphRef G = glyph_ref(L, g);
     const int N = G.N, P = N + 1;
     const int64_t ncell = 6LL * P * P;
+    const int64_t c_end = min(ncell, (int64_t)(blk + 1) * BOUNDS_PER_BLOCK);
     float best = 0.0f;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t c = (int64_t)blk * BOUNDS_PER_BLOCK + threadIdx.x; c < c_end; c += blockDim.x) {
         const int f = (int)(c / ((int64_t)P * P)), rem = (int)(c % ((int64_t)P * P)), j = rem / P, i = rem % P;
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
         for (int corner = 0; corner < 4; ++corner) {
@@ -534,19 +621,23 @@ __global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, int g_ba
         best = fmaxf(best, m0 + 0.25f * (m1 + m2) + 0.0625f * m3);
     }
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(rmax + g), __float_as_int(best));
+    if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) best = fmaxf(best, warp_best[w]);
+        // non-negative floats order like their bit patterns
+        atomicMax(reinterpret_cast<int*>(rmax + g), __float_as_int(best));
+    }
 }
 
-cudaError_t launch_bounds(const LutView& L, float* rmax, int max_N, cudaStream_t s)
+cudaError_t launch_bounds(const LutView& L, float* rmax, const Sizes& sz, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(rmax, 0, sizeof(float) * (size_t)L.n_glyphs, s);
     if (e != cudaSuccess) return e;
-    const int64_t ncell = 6LL * (max_N + 1) * (max_N + 1);
-    int64_t bx = (ncell + 255) / 256;
-    if (bx > 4096) bx = 4096;
-    for (int g0 = 0; g0 < L.n_glyphs; g0 += 65535)
-        k_bounds<<<dim3((unsigned)bx, min(65535, L.n_glyphs - g0)), 256, 0, s>>>(L, rmax, g0);
-    return cudaGetLastError();
+    auto blocks = [](int N) { return (6LL * (N + 1) * (N + 1) + BOUNDS_PER_BLOCK - 1) / BOUNDS_PER_BLOCK; };
+    return for_each_glyph_chunk(sz, blocks, [&](unsigned bx, unsigned bz, const auto& map) {
+        k_bounds<<<dim3(bx, 1, bz), 256, 0, s>>>(L, rmax, map);
+    });
 }
 
 // ------------------------------------------------------------------------------------------

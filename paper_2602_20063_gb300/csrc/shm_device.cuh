@@ -36,7 +36,8 @@ struct LutView {
 
 __host__ __device__ __forceinline__ int64_t records_per_glyph(int N, int layout)
 {
-    const int64_t P = (layout == SHM_LAYOUT_CELL) ? (int64_t)N + 1 : (int64_t)N + 2;
+    const int64_t P = (layout == SHM_LAYOUT_CELL) ? (int64_t)N + 1
+                      : (layout == SHM_LAYOUT_VALUE) ? (int64_t)N + 4 : (int64_t)N + 2;
     return 6 * P * P;
 }
 
@@ -307,6 +308,144 @@ __device__ __forceinline__ bool query_one(const LutView& L, const GlyphRef& G, f
 }
 
 // ------------------------------------------------------------------------------------------
+// Value-only reconstruction baselines (§4.2, §4.5) on a SHM_LAYOUT_VALUE table: one scalar per
+// texel, [6][N+4][N+4], entry (ii, jj) = texel (ii-1, jj-1), texel i at x = uN + 1/2 = i.
+template <int DT>
+__device__ __forceinline__ float load_val(const void* base, int64_t idx)
+{
+    if (DT == SHM_F32) return __ldg(reinterpret_cast<const float*>(base) + idx);
+    if (DT == SHM_F16) return __half2float(__ldg(reinterpret_cast<const __half*>(base) + idx));
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(base) + idx));
+}
+
+template <int DT>
+struct ValueFace {
+    const void* data;
+    int64_t base;  // entry (0, 0) of the face = texel (-1, -1)
+    int S;
+    __device__ __forceinline__ float operator()(int i, int j) const
+    {
+        return load_val<DT>(data, base + (int64_t)(j + 1) * S + (i + 1));
+    }
+};
+
+// Catmull-Rom weights of taps i-1 .. i+2 at local coordinate s, and their s-derivatives.
+__device__ __forceinline__ void catmull_rom(float s, float w[4], float dw[4])
+{
+    const float s2 = s * s, s3 = s2 * s;
+    w[0] = 0.5f * (-s3 + 2.0f * s2 - s);
+    w[1] = 0.5f * (3.0f * s3 - 5.0f * s2 + 2.0f);
+    w[2] = 0.5f * (-3.0f * s3 + 4.0f * s2 + s);
+    w[3] = 0.5f * (s3 - s2);
+    dw[0] = 0.5f * (-3.0f * s2 + 4.0f * s - 1.0f);
+    dw[1] = 0.5f * (9.0f * s2 - 10.0f * s);
+    dw[2] = 0.5f * (-9.0f * s2 + 8.0f * s + 1.0f);
+    dw[3] = 0.5f * (3.0f * s2 - 2.0f * s);
+}
+
+// Uniform cubic B-spline weights of taps i-1 .. i+2 (any s: the cell's polynomial).
+__device__ __forceinline__ void bspline3(float s, float w[4])
+{
+    const float r = 1.0f - s, s2 = s * s, s3 = s2 * s;
+    w[0] = r * r * r * (1.0f / 6.0f);
+    w[1] = (3.0f * s3 - 6.0f * s2 + 4.0f) * (1.0f / 6.0f);
+    w[2] = (-3.0f * s3 + 3.0f * s2 + 3.0f * s + 1.0f) * (1.0f / 6.0f);
+    w[3] = s3 * (1.0f / 6.0f);
+}
+
+template <int DT>
+__device__ __forceinline__ float tensor16(const ValueFace<DT>& V, int i, int j, const float wu[4], const float wv[4])
+{
+    float acc = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float row = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) row = fmaf(wu[a], V(i - 1 + a, j - 1 + b), row);
+        acc = fmaf(wv[b], row, acc);
+    }
+    return acc;
+}
+
+template <int DT>
+__device__ __forceinline__ float bilinear_at(const ValueFace<DT>& V, int i, int j, float s, float t)
+{
+    const float a = V(i, j), b = V(i + 1, j), c = V(i, j + 1), d = V(i + 1, j + 1);
+    const float lo = fmaf(s, b - a, a), hi = fmaf(s, d - c, c);
+    return fmaf(t, hi - lo, lo);
+}
+
+// Cubic B-spline value at cell (k, l) shifted by (di, dj) texels, the cell clamped to [0, N]
+// and the local coordinate carried along.
+template <int DT>
+__device__ __forceinline__ float bspline_at(const ValueFace<DT>& V, int N, int i, int j, float s, float t)
+{
+    const int ic = min(max(i, 0), N), jc = min(max(j, 0), N);
+    float wu[4], wv[4];
+    bspline3(s + (float)(i - ic), wu);
+    bspline3(t + (float)(j - jc), wv);
+    return tensor16(V, ic, jc, wu, wv);
+}
+
+template <int METHOD, int DT>
+__device__ __forceinline__ bool recon_one(const LutView& L, const GlyphRef& G, float d0, float d1, float d2,
+                                          QueryResult& out, Chart& c)
+{
+    if (!chart_of(d0, d1, d2, c)) return false;
+    const int N = G.N;
+    int i, j;
+    float s, t;
+    cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, N, i, s);
+    cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, N, j, t);
+    const int S = N + 4;
+    const ValueFace<DT> V{L.data, G.base + (int64_t)c.f * S * S, S};
+    const float hN = 0.5f * (float)N;
+    float r, Ru = 0.0f, Rv = 0.0f;
+    if (METHOD == SHM_RECON_NEAREST) {
+        i = min(max(i + (s >= 0.5f ? 1 : 0), 1), N);
+        j = min(max(j + (t >= 0.5f ? 1 : 0), 1), N);
+        r = V(i, j);
+    } else if (METHOD == SHM_RECON_BILINEAR) {
+        r = bilinear_at(V, i, j, s, t);
+        Ru = (bilinear_at(V, i + 1, j, s, t) - bilinear_at(V, i - 1, j, s, t)) * hN;
+        Rv = (bilinear_at(V, i, j + 1, s, t) - bilinear_at(V, i, j - 1, s, t)) * hN;
+    } else if (METHOD == SHM_RECON_BICUBIC) {
+        float wu[4], dwu[4], wv[4], dwv[4];
+        catmull_rom(s, wu, dwu);
+        catmull_rom(t, wv, dwv);
+        float acc = 0.0f, au = 0.0f, av = 0.0f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float row = 0.0f, drow = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float v = V(i - 1 + a, j - 1 + b);
+                row = fmaf(wu[a], v, row);
+                drow = fmaf(dwu[a], v, drow);
+            }
+            acc = fmaf(wv[b], row, acc);
+            au = fmaf(wv[b], drow, au);
+            av = fmaf(dwv[b], row, av);
+        }
+        r = acc;
+        Ru = (float)N * au;
+        Rv = (float)N * av;
+    } else {
+        r = bspline_at(V, N, i, j, s, t);
+        Ru = (bspline_at(V, N, i + 1, j, s, t) - bspline_at(V, N, i - 1, j, s, t)) * hN;
+        Rv = (bspline_at(V, N, i, j + 1, s, t) - bspline_at(V, N, i, j - 1, s, t)) * hN;
+    }
+    out.R = G.r0 + r;
+    out.Ru = Ru;
+    out.Rv = Rv;
+    out.grad = s2_gradient(c, Ru, Rv);
+    out.f = c.f;
+    out.i = i;
+    out.j = j;
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
 // Generic record store / load for any dtype and layout.
 __device__ __forceinline__ uint2 f4_to_h4(float4 v)
 {
@@ -325,6 +464,13 @@ __device__ __forceinline__ void store_rec(void* data, int dtype, int64_t rec, fl
     if (dtype == SHM_F32) reinterpret_cast<float4*>(data)[rec] = v;
     else if (dtype == SHM_F16) reinterpret_cast<uint2*>(data)[rec] = f4_to_h4(v);
     else reinterpret_cast<uint2*>(data)[rec] = f4_to_b4(v);
+}
+
+__device__ __forceinline__ void store_val(void* data, int dtype, int64_t idx, float v)
+{
+    if (dtype == SHM_F32) reinterpret_cast<float*>(data)[idx] = v;
+    else if (dtype == SHM_F16) reinterpret_cast<__half*>(data)[idx] = __float2half_rn(v);
+    else reinterpret_cast<__nv_bfloat16*>(data)[idx] = __float2bfloat16_rn(v);
 }
 
 __device__ __forceinline__ float4 load_rec_any(const void* data, int dtype, int64_t rec)

@@ -3,10 +3,91 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <type_traits>
+#include <vector>
+
 #include "../../include/shm.h"
 #include "shm_device.cuh"
 
 namespace shm {
+
+// ------------------------------------------------------------------------------------------
+// Per-glyph block grids.  A pool with per-glyph resolutions would need max-N-sized grids per
+// glyph, most of whose blocks exit at once (512 glyphs of N in {16..128}: ~60 % empty blocks).
+// Instead the host, which reads the resolutions anyway, passes a prefix of per-glyph block counts
+// by value (a __grid_constant__ kernel parameter of up to ~8 KB), and each block finds its glyph
+// by a block-uniform binary search; the grid is exactly the work.  Uniform pools keep a
+// (blocks, faces, glyphs) grid.
+struct Sizes {
+    int G;
+    int N_uniform;              // > 0: every glyph has this N
+    const int32_t* N_host;      // otherwise: host copy of the per-glyph N
+    int max_N;
+};
+
+constexpr int TILEMAP_MAX = 2000;
+
+struct UniformMap {
+    int32_t g0;
+};
+
+struct TileMap {
+    int32_t g0, n;
+    int32_t cum[TILEMAP_MAX + 1];  // cum[k]: first block of glyph g0 + k; cum[n]: blocks in this launch
+};
+
+__device__ __forceinline__ int map_block(const UniformMap& m, int& local)
+{
+    local = blockIdx.x;
+    return m.g0 + blockIdx.z;
+}
+
+__device__ __forceinline__ int map_block(const TileMap& m, int& local)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = m.n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (m.cum[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    local = b - m.cum[lo];
+    return m.g0 + lo;
+}
+
+// Calls launch(grid_x, grid_z, map) once per chunk of glyphs, with blocks_of(N) blocks per glyph
+// along x.  Glyphs with zero blocks are skipped by the search (equal prefixes).
+template <class BlocksOf, class Launch>
+cudaError_t for_each_glyph_chunk(const Sizes& sz, BlocksOf blocks_of, Launch launch)
+{
+    if (sz.N_uniform > 0) {
+        const int64_t b = blocks_of(sz.N_uniform);
+        if (b <= 0) return cudaSuccess;
+        if (b > 0x7fffffff) return cudaErrorInvalidConfiguration;
+        for (int g0 = 0; g0 < sz.G; g0 += 65535)
+            launch((unsigned)b, (unsigned)(sz.G - g0 < 65535 ? sz.G - g0 : 65535), UniformMap{g0});
+        return cudaGetLastError();
+    }
+    std::unique_ptr<TileMap> m(new TileMap);
+    for (int g0 = 0; g0 < sz.G;) {
+        m->g0 = g0;
+        m->cum[0] = 0;
+        int n = 0;
+        int64_t total = 0;
+        while (g0 + n < sz.G && n < TILEMAP_MAX) {
+            const int64_t b = blocks_of(sz.N_host[g0 + n]);
+            if (n > 0 && total + b > 0x7fffffff) break;
+            if (b > 0x7fffffff) return cudaErrorInvalidConfiguration;
+            total += b;
+            m->cum[++n] = (int32_t)total;
+        }
+        m->n = n;
+        if (total > 0) launch((unsigned)total, 1u, *m);
+        g0 += n;
+    }
+    return cudaGetLastError();
+}
 
 struct QueryArgs {
     LutView L;
@@ -60,9 +141,13 @@ cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* 
                             cudaStream_t s);
 cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
                                 cudaStream_t s);
-cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, int max_N, cudaStream_t s);
-cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, int max_N, cudaStream_t s);
-cudaError_t launch_bounds(const LutView& L, float* rmax, int max_N, cudaStream_t s);
+cudaError_t launch_sh_value(const LutView& out, void* data, int L, const float* coeffs, cudaStream_t s);
+cudaError_t launch_query_recon(const QueryArgs& a, int method, cudaStream_t s);
+cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, const Sizes& sz, cudaStream_t s);
+cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, const Sizes& sz, cudaStream_t s);
+cudaError_t launch_bounds(const LutView& L, float* rmax, const Sizes& sz, cudaStream_t s);
+cudaError_t launch_mip(const LutView& fine, const LutView& coarse, void* cdata, int32_t* dev_status,
+                       const Sizes& coarse_sz, cudaStream_t s);
 cudaError_t launch_sh_eval(int L, int G, const float* coeffs, int64_t Q, const float* dirs, const int32_t* glyph,
                            const int64_t* seg, float* R, float* grad, float* normal, int32_t* dev_status,
                            cudaStream_t s);

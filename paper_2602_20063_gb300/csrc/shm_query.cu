@@ -1,201 +1,20 @@
-// Forward query kernel: direction -> face/uv -> 2x2 texel fetch -> Hermite value + chart
-// gradient -> S^2 gradient -> normal (arXiv 2602.20063, §3.2-§3.4).
-//
-// One thread per query; warps cover 32 consecutive queries so direction loads and output stores
-// stay coalesced; for CSR segments one binary search per warp and chunk finds the glyph of the
-// warp's first query and each lane then walks forward.
-// The path is bound by HBM bandwidth: 12 B of direction, 4 corner records (64 B f32 / 32 B
-// 16-bit) and 28 B of outputs per query against ~250 flops.
-#include "shm_internal.h"
+// Hermite query dispatch (§3.2-§3.4): dtype x layout instances of the query kernel skeleton.
+#include "shm_query_kernel.cuh"
 
 namespace shm {
-
-constexpr int QBLOCK = 512;      // threads per CTA
-constexpr int QIT = 8;           // iterations per CTA chunk: a CTA takes QBLOCK * QIT = 4,096 consecutive queries
-constexpr int QMINBLOCKS = 2;    // <= 64 registers; 32 resident warps per SM
-
-// Work is handed out per CTA in contiguous chunks of 4,096 queries, so that for per-glyph query
-// segments a CTA serves whole glyphs and the glyph's table stays in that SM's L1 (two CTAs per SM
-// keep two tables of up to ~110 KB resident) instead of being pulled into several SMs.
-//
-// VEC (all of dirs / grad / normal 16-byte aligned): for a full warp round (32 queries) the 384 B
-// of directions are read with 24 128-bit loads and the 384 B of gradients and of normals are
-// written with 24 128-bit stores, re-distributed through a 384-byte per-warp shared buffer, so a
-// warp issues 1 + 4 + 3 global memory instructions per round instead of 3 + 4 + 7 (the load/store
-// queue, not DRAM, limited the random-access case).  Partial rounds use scalar accesses.
-template <int DT, int LAYOUT, bool VEC>
-__global__ void __launch_bounds__(QBLOCK, QMINBLOCKS) k_query_fwd(QueryArgs a)
-{
-    __shared__ __align__(16) float sbuf[QBLOCK / 32][96];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* wb = sbuf[warp];
-    const int64_t CH = (int64_t)QBLOCK * QIT;
-    const int G = a.L.n_glyphs;
-    uint32_t status = 0;
-    const float qnan = __int_as_float(0x7fc00000);
-    const float4* dirs4 = reinterpret_cast<const float4*>(a.dirs);
-
-    for (int64_t c0 = (int64_t)blockIdx.x * CH; c0 < a.Q; c0 += (int64_t)gridDim.x * CH) {
-        // glyph of this lane's first query and the end of its segment (one search per warp and chunk)
-        int g = 0;
-        int64_t seg_end = INT64_MAX;
-        const int64_t qw0 = c0 + warp * 32;
-        if (a.seg) {
-            int g0 = 0;
-            long long e0 = 0;
-            if (lane == 0 && qw0 < a.Q) {
-                g0 = (qw0 < __ldg(a.seg)) ? -1 : seg_find(a.seg, G, qw0);
-                e0 = (g0 >= 0 && g0 < G) ? __ldg(a.seg + g0 + 1) : 0;
-            }
-            g = __shfl_sync(0xffffffffu, g0, 0);
-            seg_end = __shfl_sync(0xffffffffu, e0, 0);
-        }
-        // direction of the first round: vector (full round) or scalar
-        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
-        float n0 = 0.f, n1 = 0.f, n2 = 0.f;
-        if (VEC && qw0 + 32 <= a.Q) {
-            if (lane < 24) pv = __ldg(dirs4 + (3 * qw0) / 4 + lane);
-        } else if (qw0 + lane < a.Q) {
-            const int64_t q = qw0 + lane;
-            n0 = __ldg(a.dirs + 3 * q); n1 = __ldg(a.dirs + 3 * q + 1); n2 = __ldg(a.dirs + 3 * q + 2);
-        }
-#pragma unroll 1
-        for (int it = 0; it < QIT; ++it) {
-            const int64_t qw = qw0 + (int64_t)it * QBLOCK;
-            if (qw >= a.Q) break;
-            const bool full = VEC && (qw + 32 <= a.Q);
-            const int64_t q = qw + lane;
-            float d0, d1, d2;
-            if (full) {
-                // re-distribute the warp's 24 float4 of directions: lane L takes floats 3L..3L+2
-                if (lane < 24) reinterpret_cast<float4*>(wb)[lane] = pv;
-                __syncwarp();
-                d0 = wb[3 * lane]; d1 = wb[3 * lane + 1]; d2 = wb[3 * lane + 2];
-                __syncwarp();
-            } else {
-                if (q >= a.Q) break;
-                d0 = n0; d1 = n1; d2 = n2;
-            }
-            // prefetch the next round's directions: the latency overlaps the table fetch below
-            if (it + 1 < QIT) {
-                const int64_t qn = qw + QBLOCK;
-                if (VEC && qn + 32 <= a.Q) {
-                    if (lane < 24) pv = __ldg(dirs4 + (3 * qn) / 4 + lane);
-                } else if (qn + lane < a.Q) {
-                    n0 = __ldg(a.dirs + 3 * (qn + lane));
-                    n1 = __ldg(a.dirs + 3 * (qn + lane) + 1);
-                    n2 = __ldg(a.dirs + 3 * (qn + lane) + 2);
-                }
-            }
-            int gq = 0;
-            if (a.glyph) {
-                gq = __ldg(a.glyph + q);
-            } else if (a.seg) {
-                if (q >= seg_end || g < 0) {
-                    if (g < 0 && q >= __ldg(a.seg)) g = 0;
-                    while (g >= 0 && g < G && q >= __ldg(a.seg + g + 1)) ++g;
-                    seg_end = (g >= 0 && g < G) ? __ldg(a.seg + g + 1) : INT64_MAX;
-                }
-                gq = g;
-            }
-            bool valid = true;
-            if (gq < 0 || gq >= G) { valid = false; status |= SHM_DEV_BOUNDS; }
-            QueryResult r;
-            Chart c;
-            if (valid) {
-                const GlyphRef Gr = glyph_ref(a.L, gq);
-                valid = query_one<DT, LAYOUT>(a.L, Gr, d0, d1, d2, r, c);
-                if (!valid) status |= SHM_DEV_NONFINITE;
-            }
-            if (!valid) {
-                r.R = r.Ru = r.Rv = qnan;
-                r.grad = Vec3{qnan, qnan, qnan};
-                r.f = r.i = r.j = -1;
-            }
-            const Vec3 n = (a.normal && valid) ? surface_normal(d0, d1, d2, r.R, r.grad) : Vec3{qnan, qnan, qnan};
-            if (a.R) a.R[q] = r.R;
-            if (full) {
-                if (a.grad) {
-                    wb[3 * lane] = r.grad.x; wb[3 * lane + 1] = r.grad.y; wb[3 * lane + 2] = r.grad.z;
-                    __syncwarp();
-                    if (lane < 24) reinterpret_cast<float4*>(a.grad)[(3 * qw) / 4 + lane] = reinterpret_cast<const float4*>(wb)[lane];
-                    __syncwarp();
-                }
-                if (a.normal) {
-                    wb[3 * lane] = n.x; wb[3 * lane + 1] = n.y; wb[3 * lane + 2] = n.z;
-                    __syncwarp();
-                    if (lane < 24) reinterpret_cast<float4*>(a.normal)[(3 * qw) / 4 + lane] = reinterpret_cast<const float4*>(wb)[lane];
-                    __syncwarp();
-                }
-            } else {
-                if (a.grad) {
-                    a.grad[3 * q] = r.grad.x;
-                    a.grad[3 * q + 1] = r.grad.y;
-                    a.grad[3 * q + 2] = r.grad.z;
-                }
-                if (a.normal) {
-                    a.normal[3 * q] = n.x;
-                    a.normal[3 * q + 1] = n.y;
-                    a.normal[3 * q + 2] = n.z;
-                }
-            }
-            if (a.chart) {
-                a.chart[2 * q] = r.Ru;
-                a.chart[2 * q + 1] = r.Rv;
-            }
-            if (a.fij) {
-                a.fij[3 * q] = r.f;
-                a.fij[3 * q + 1] = r.i;
-                a.fij[3 * q + 2] = r.j;
-            }
-        }
-    }
-    report_status(a.dev_status, status);
-}
-
-template <int DT, int LAYOUT, bool VEC>
-static cudaError_t launch_fwd_v(const QueryArgs& a, cudaStream_t s)
-{
-    // one persistent wave: SMs x resident blocks per SM
-    static int resident = 0;
-    if (resident == 0) {
-        int r = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_query_fwd<DT, LAYOUT, VEC>, QBLOCK, 0) != cudaSuccess ||
-            r < 1)
-            r = QMINBLOCKS;
-        resident = r;
-    }
-    int64_t blocks = (a.Q + (int64_t)QBLOCK * QIT - 1) / ((int64_t)QBLOCK * QIT);
-    const int64_t cap = (int64_t)sm_count() * resident;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_query_fwd<DT, LAYOUT, VEC><<<(unsigned)blocks, QBLOCK, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-// The vector I/O path measured 4 % faster on uniform random queries of one large table and 7 %
-// slower on per-glyph CSR segments (GB300, 2^28 planet queries / 2^26 glyph-field queries), so it
-// is used when there are no segments and the buffers are 16-byte aligned.
-template <int DT, int LAYOUT>
-static cudaError_t launch_fwd_t(const QueryArgs& a, cudaStream_t s)
-{
-    const auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-    if (!a.seg && al16(a.dirs) && al16(a.grad) && al16(a.normal)) return launch_fwd_v<DT, LAYOUT, true>(a, s);
-    return launch_fwd_v<DT, LAYOUT, false>(a, s);
-}
 
 cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s)
 {
     if (a.Q == 0) return cudaSuccess;
     const int dt = a.L.dtype, ly = a.L.layout;
     if (ly == SHM_LAYOUT_TEXEL) {
-        if (dt == SHM_F32) return launch_fwd_t<SHM_F32, SHM_LAYOUT_TEXEL>(a, s);
-        if (dt == SHM_F16) return launch_fwd_t<SHM_F16, SHM_LAYOUT_TEXEL>(a, s);
-        return launch_fwd_t<SHM_BF16, SHM_LAYOUT_TEXEL>(a, s);
+        if (dt == SHM_F32) return launch_fwd_t<SHM_F32, SHM_LAYOUT_TEXEL, -1>(a, s);
+        if (dt == SHM_F16) return launch_fwd_t<SHM_F16, SHM_LAYOUT_TEXEL, -1>(a, s);
+        return launch_fwd_t<SHM_BF16, SHM_LAYOUT_TEXEL, -1>(a, s);
     }
-    if (dt == SHM_F32) return launch_fwd_t<SHM_F32, SHM_LAYOUT_CELL>(a, s);
-    if (dt == SHM_F16) return launch_fwd_t<SHM_F16, SHM_LAYOUT_CELL>(a, s);
-    return launch_fwd_t<SHM_BF16, SHM_LAYOUT_CELL>(a, s);
+    if (dt == SHM_F32) return launch_fwd_t<SHM_F32, SHM_LAYOUT_CELL, -1>(a, s);
+    if (dt == SHM_F16) return launch_fwd_t<SHM_F16, SHM_LAYOUT_CELL, -1>(a, s);
+    return launch_fwd_t<SHM_BF16, SHM_LAYOUT_CELL, -1>(a, s);
 }
 
 }  // namespace shm
