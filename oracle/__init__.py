@@ -36,7 +36,8 @@ class Camera(C.Structure):
 class RaycastParams(C.Structure):
     _fields_ = [("march", C.c_int), ("bisect", C.c_int), ("newton", C.c_int),
                 ("ambient", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
-                ("shininess", C.c_double), ("light", C.c_double * 3)]
+                ("shininess", C.c_double), ("light", C.c_double * 3),
+                ("lod", C.c_int), ("bisect_min", C.c_int), ("newton_min", C.c_int)]
 
 
 class QueryOut(C.Structure):
@@ -325,6 +326,14 @@ def bake_sh_vjp(N, L, dlut):
     return dc
 
 
+def lod_steps(cam, prm, centre, rmax):
+    """(bisection steps, Newton steps, projected radius in pixels) of one object."""
+    b, n, p = C.c_int(), C.c_int(), C.c_float()
+    c = _c64(centre)
+    lib().shmo_lod_steps(C.byref(cam), C.byref(prm), _p(c, _d), C.c_double(rmax), C.byref(b), C.byref(n), C.byref(p))
+    return b.value, n.value, p.value
+
+
 # ----------------------------------------------------------------- value-only baselines (§4.2, §4.5)
 RECON_NEAREST, RECON_BILINEAR, RECON_BICUBIC, RECON_FAST_BICUBIC = 0, 1, 2, 3
 
@@ -416,9 +425,10 @@ def make_camera(eye, fwd, right, up, fov_y_deg, W, H):
 
 
 def make_raycast_params(march=32, bisect=12, newton=3, ambient=0.1, kd=0.7, ks=0.3, shininess=64.0,
-                        light=(1.0, 1.0, 1.0)):
+                        light=(1.0, 1.0, 1.0), lod=0, bisect_min=8, newton_min=2):
     p = RaycastParams()
     p.march, p.bisect, p.newton = march, bisect, newton
+    p.lod, p.bisect_min, p.newton_min = lod, bisect_min, newton_min
     p.ambient, p.kd, p.ks, p.shininess = ambient, kd, ks, shininess
     for q in range(3):
         p.light[q] = light[q]

@@ -130,7 +130,10 @@ typedef struct {
     int march, bisect, newton;
     double ambient, kd, ks, shininess;
     double light[3];
+    int lod, bisect_min, newton_min; /* projected-size refinement allocation (§3.1); lod = 0: fixed */
 } shmo_raycast_params;
+void shmo_lod_steps(const shmo_camera* cam, const shmo_raycast_params* prm, const double centre[3], double rmax,
+                    int* bisect, int* newton, float* p_px);
 void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* Ns, const double* r0,
                         int n_obj, const double* centre, const double* scale, const double* rmax,
                         const int32_t* glyph, const shmo_camera* cam, const shmo_raycast_params* prm,

@@ -20,6 +20,13 @@
  *
  * Camera: d = normalise(fwd + x_ndc tan(fov_y/2) (W/H) right + y_ndc tan(fov_y/2) up) with
  * x_ndc = 2(px + 1/2)/W - 1 and y_ndc = 1 - 2(py + 1/2)/H.
+ *
+ * Refinement allocation by projected size (§3.1: more refinement iterations for glyphs that are
+ * large on screen; the paper gives no rule).  Reading: projected radius p = R_max (H/2) /
+ * (|c - o| tan(fov_y/2)) pixels; bisection steps = the fewest b in [bisect_min, bisect] with
+ * M 2^b >= 128 p, i.e. the marched bracket 2 R_max / M shrinks below 1/64 pixel (b = bisect if
+ * none does); Newton steps = newton if p >= 64 pixels, else newton_min.  p decides integers, so it is
+ * formed in float32, operation by operation in the order written (the device does the same).
  */
 #include <math.h>
 #include "oracle.h"
@@ -47,6 +54,28 @@ static void surface_F(const lut_ref* L, int g, double scale, const double c[3], 
         double dg = d[0] * qo->grad[0] + d[1] * qo->grad[1] + d[2] * qo->grad[2];
         *dF = dw - scale * sg * dg / dist;
     }
+}
+
+void shmo_lod_steps(const shmo_camera* cam, const shmo_raycast_params* prm, const double centre[3], double rmax,
+                    int* bisect, int* newton, float* p_px)
+{
+    *bisect = prm->bisect;
+    *newton = prm->newton;
+    if (!prm->lod) { if (p_px) *p_px = NAN; return; }
+    float dx = (float)centre[0] - (float)cam->eye[0];
+    float dy = (float)centre[1] - (float)cam->eye[1];
+    float dz = (float)centre[2] - (float)cam->eye[2];
+    float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    float D = sqrtf((xx + yy) + zz);
+    float num = (float)rmax * (0.5f * (float)cam->H);
+    float den = D * (float)cam->tan_half_fov_y;
+    float p = num / den;
+    float need = 128.0f * p;
+    for (int b = prm->bisect_min; b <= prm->bisect; ++b) {
+        if ((float)prm->march * ldexpf(1.0f, b) >= need) { *bisect = b; break; }
+    }
+    *newton = (p >= 64.0f) ? prm->newton : prm->newton_min;
+    if (p_px) *p_px = p;
 }
 
 void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* Ns, const double* r0,
@@ -78,6 +107,8 @@ void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* N
         double t0 = -b - sq, t1 = -b + sq;
         if (t1 <= 0.0) continue;
         if (t0 < 0.0) t0 = 0.0;
+        int n_bisect, n_newton;
+        shmo_lod_steps(cam, prm, c, rmax[ob], &n_bisect, &n_newton, NULL);
         shmo_query_out qo;
         double F, dF;
         double lo = t0, hi = t0, thit = NAN;
@@ -99,13 +130,13 @@ void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* N
                 }
             }
             if (!found) continue;
-            for (int it = 0; it < prm->bisect; ++it) {
+            for (int it = 0; it < n_bisect; ++it) {
                 double mid = 0.5 * (lo + hi);
                 surface_F(&L, glyph[ob], scale[ob], c, o, d, mid, &F, NULL, &qo);
                 if (F < 0.0) hi = mid; else lo = mid;
             }
             double t = 0.5 * (lo + hi);
-            for (int it = 0; it < prm->newton; ++it) {
+            for (int it = 0; it < n_newton; ++it) {
                 surface_F(&L, glyph[ob], scale[ob], c, o, d, t, &F, &dF, &qo);
                 if (dF == 0.0) break;
                 double tn = t - F / dF;

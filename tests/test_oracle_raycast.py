@@ -143,3 +143,31 @@ def test_dense_march_agrees(oracle):
                     break
         agree += int(best == out["obj_id"][q])
     assert agree >= int(0.97 * W * H)
+
+
+def test_lod_refinement_allocation(oracle):
+    """§3.1 refinement by projected size (reading: fewest bisections with M 2^b >= 128 p, Newton
+    steps full from 64 px).  Checked against the closed-form projected radius and an independent
+    float32 evaluation; more iterations for larger projected objects; off -> fixed counts."""
+    W, H, fov = 1920, 1080, 45.0
+    cam = oracle.make_camera([0.0, 0.0, 30.0], [0.0, 0.0, -1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], fov, W, H)
+    off = oracle.make_raycast_params(march=32, bisect=14, newton=4, lod=0)
+    assert oracle.lod_steps(cam, off, np.zeros(3), 1.0)[:2] == (14, 4)
+    prm = oracle.make_raycast_params(march=32, bisect=16, newton=4, lod=1, bisect_min=8, newton_min=2)
+    th = np.float32(math.tan(math.radians(fov / 2)))
+    last = (0, 0)
+    for D in (200.0, 100.0, 40.0, 20.0, 10.0, 5.0, 2.5, 1.2):
+        rmax = 1.1
+        b, n, p = oracle.lod_steps(cam, prm, np.array([0.0, 0.0, 30.0 - D]), rmax)
+        assert abs(p - rmax * H / 2 / (D * math.tan(math.radians(fov / 2)))) <= 1e-5 * p
+        f32 = np.float32
+        dz = f32(30.0 - D) - f32(30.0)
+        D32 = np.sqrt((f32(0.0) + f32(0.0)) + dz * dz, dtype=np.float32)
+        p32 = (f32(rmax) * f32(0.5 * H)) / (D32 * th)
+        assert p == p32
+        want = next((k for k in range(8, 17) if 32 * 2.0 ** k >= 128 * float(p32)), 16)
+        assert b == want and 8 <= b <= 16
+        assert n == (4 if p >= 64 else 2)
+        assert (b, n) >= last
+        last = (b, n)
+    assert last[0] >= 12 and last[1] == 4   # a close object gets the most refinement
