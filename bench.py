@@ -253,7 +253,7 @@ class GlyphField:
             "query_fwd": {"bound": "hbm", "algorithmic": q_alg, "unit": "GB/s", "peak": peaks["hbm_gbs"],
                           "per_unit": f"{q_alg / self.Q:.1f} B/query = table bytes once ({lut_bytes / self.Q:.1f} B/q) "
                                       "+ 12 B direction + 28 B outputs (compulsory traffic)",
-                          "files": ["paper_2602_20063_gb300/csrc/shm_query.cu",
+                          "files": ["paper_2602_20063_gb300/csrc/shm_query_staged.cu",
                                     "paper_2602_20063_gb300/csrc/shm_device.cuh"]},
             "sh_build_gemm": ({"bound": "alu", "algorithmic": 2.0 * self.G * K * 4 * T, "unit": "TFLOP/s",
                                "peak": fp32_simt_peak_tflops(peaks, sms),
@@ -469,7 +469,7 @@ class Planet:
         rec = self.S.record_bytes(self.dtype, self.layout) * (1 if self.layout == 1 else 4)
         per_q = rec + 12 + 28
         T = 6 * (self.N + 2) ** 2
-        qfiles = ["paper_2602_20063_gb300/csrc/shm_query.cu", "paper_2602_20063_gb300/csrc/shm_device.cuh"]
+        qfiles = ["paper_2602_20063_gb300/csrc/shm_query_kernel.cuh", "paper_2602_20063_gb300/csrc/shm_device.cuh"]
         return {
             "query_random": {"bound": "hbm", "algorithmic": self.Qr * per_q, "unit": "GB/s", "peak": peaks["hbm_gbs"],
                              "per_unit": f"{per_q} B/query: 4 corner records ({rec} B, the paper's 16-scalar "
@@ -658,11 +658,33 @@ class Impostors:
         return {}
 
     def extras(self, S, torch, steps):
-        S.raycast(self.lut, self.objs, self.n, self.cam, self.prm, ws=self.ws, out=self.out)
-        torch.cuda.synchronize()
-        nq = S.raycast_query_count(self.ws)
+        """Surface queries per frame, and the ray cast alone with fixed refinement counts against
+        refinement by projected size (§3.1; bisection 8-16, Newton 2-4 as in the paper)."""
+        st = torch.cuda.current_stream()
+
+        def timed(prm, n=5):
+            S.raycast(self.lut, self.objs, self.n, self.cam, prm, ws=self.ws, out=self.out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(n):
+                S.raycast(self.lut, self.objs, self.n, self.cam, prm, ws=self.ws, out=self.out)
+            e1.record(st)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / n, S.raycast_query_count(self.ws)
+
+        ms_fixed, nq = timed(self.prm)
         hit = float((self.out["obj_id"] >= 0).float().mean())
-        return {"surface_queries_per_frame": nq, "hit_fraction": hit}
+        depth_fixed = self.out["depth"].clone()
+        lod = S.make_raycast_params(bisect=16, newton=4, lod=1, bisect_min=8, newton_min=2)
+        ms_lod, nq_lod = timed(lod)
+        both = torch.isfinite(depth_fixed) & torch.isfinite(self.out["depth"])
+        ddepth = float(((self.out["depth"] - depth_fixed).abs() / depth_fixed)[both].max()) if both.any() else 0.0
+        return {"surface_queries_per_frame": nq, "hit_fraction": hit,
+                "raycast_fixed": {"ms": round(ms_fixed, 4), "surface_queries": nq,
+                                  "params": "march 32, bisect 12, Newton 3 for every object"},
+                "raycast_lod": {"ms": round(ms_lod, 4), "surface_queries": nq_lod,
+                                "params": "march 32, bisect 8-16 (march 2^b >= 128 p), Newton 4 from 64 px else 2",
+                                "max_rel_depth_change_vs_fixed": ddepth}}
 
     def oracle_measure(self, budget_s, procs):
         """Oracle rate projected to one impostor step: FP64 FD bake of all 512 objects (spawned

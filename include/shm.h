@@ -274,10 +274,19 @@ typedef struct {
 
 typedef struct {
     int32_t march;  /* uniform F samples over the bounding-sphere chord (>= 1) */
-    int32_t bisect; /* bisection steps after the first sign change */
-    int32_t newton; /* Newton-Raphson steps after bisection */
+    int32_t bisect; /* bisection steps after the first sign change (the maximum when lod != 0) */
+    int32_t newton; /* Newton-Raphson steps after bisection (the maximum when lod != 0) */
     float ambient, kd, ks, shininess;
     float light[3];
+    /* Refinement by projected size (§3.1: more iterations for glyphs large on screen; the paper
+     * gives no rule).  lod != 0: per object, p = R_max (H/2) / (|c - eye| tan(fov_y/2)) pixels,
+     * computed in float32 in that order without fused operations; bisection steps = the fewest b
+     * in [bisect_min, bisect] with march * 2^b >= 128 p (the marched bracket 2 R_max / march
+     * falls below 1/64 pixel; bisect if none does); Newton steps = newton if p >= 64, else
+     * newton_min.  lod == 0: bisect and newton for every object. */
+    int32_t lod;
+    int32_t bisect_min;
+    int32_t newton_min;
 } shm_raycast_params;
 
 typedef struct {

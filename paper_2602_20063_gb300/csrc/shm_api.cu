@@ -381,7 +381,9 @@ shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj
     if (!cam || !prm || n_obj < 0 || (n_obj > 0 && !objs)) return SHM_ERR_INVALID_ARG;
     if (cam->W <= 0 || cam->H <= 0 || cam->W > 65536 || cam->H > 65536) return SHM_ERR_INVALID_ARG;
     if (prm->march < 1 || prm->march > 4096 || prm->bisect < 0 || prm->bisect > 64 || prm->newton < 0 ||
-        prm->newton > 64)
+        prm->newton > 64 ||
+        (prm->lod && (prm->bisect_min < 0 || prm->bisect_min > prm->bisect || prm->newton_min < 0 ||
+                      prm->newton_min > prm->newton)))
         return SHM_ERR_INVALID_ARG;
     const int64_t need = raycast_workspace_bytes(n_obj, cam->W, cam->H);
     if (need > 0 && (!ws || (int64_t)ws_bytes < need)) return SHM_ERR_WORKSPACE;

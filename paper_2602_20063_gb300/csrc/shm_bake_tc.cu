@@ -14,11 +14,16 @@
 // leaving a relative error ~2^-21 per product, below the float32 accumulation error of K terms.
 //
 // Schedule: persistent CTAs (one per SM, 256 threads), tiles of 128 columns x 256 glyphs, K in
-// chunks of 16 (64 B rows, 64-byte swizzle), 4 smem stages of 48 KB so TMA runs several chunks
-// ahead of the MMAs, 2 TMEM accumulators of 256 columns (512 columns, the whole TMEM) so the
-// epilogue of one tile overlaps the MMAs of the next.
+// chunks of 16 (64 B rows, 64-byte swizzle), 3 smem stages of 48 KB so TMA runs chunks ahead of
+// the MMAs, 2 TMEM accumulators of 256 columns (512 columns, the whole TMEM) so the epilogue of
+// one tile overlaps the MMAs of the next.
 //   warp 0 lane 0: TMA producer        warp 1: TMEM allocation; lane 0 issues the MMAs
 //   warps 4-7: epilogue (TMEM lane quadrant = warp % 4), table writes
+// Epilogue of the float32 texel table: per 32 glyphs the four warps transpose their TMEM rows into
+// a [32 glyphs][128 columns] shared box (double-buffered) and one thread writes it with a TMA
+// tensor store (512 B contiguous per glyph row).  Plain per-thread stores, 128 B per warp
+// instruction to 32 different table rows, ran the memory write path at ~9 B/clk/SM and left the
+// tensor pipe idle 70 % of the time.  Other dtypes / layouts keep per-thread stores.
 // Every mbarrier wait is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, drains its own
 // copies and MMAs with bounded waits, frees TMEM and returns.
 #include <cuda.h>
@@ -34,12 +39,14 @@ namespace tc {
 constexpr int TM = 128;  // table columns per tile (MMA M)
 constexpr int TN = 256;  // glyphs per tile (MMA N)
 constexpr int KC = 16;   // K per stage: 16 x 4 B = one 64-byte swizzle row
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 3;
 constexpr uint32_t A_BYTES = TM * KC * 4;
 constexpr uint32_t B_BYTES = TN * KC * 4;
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int OG = 32;                                // glyphs per output store box
+constexpr uint32_t OUT_BYTES = OG * TM * 4;           // one [32 glyphs][128 columns] f32 box, 16 KB
 constexpr uint32_t BAR_BYTES = 256;
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + BAR_BYTES + 1024;
+constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 2 * OUT_BYTES + BAR_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;   // 1 s
 constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;   // 100 ms
@@ -119,6 +126,33 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y)
+{
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"((uint64_t)map), "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// AND of `ok` over the 128 epilogue threads (named barrier 1): all leave or all stay.
+__device__ __forceinline__ bool epi_all(bool ok)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)ok)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
@@ -165,11 +199,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 __global__ void __launch_bounds__(256, 1)
     k_sh_gemm_tc(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, Args a)
+                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                 const __grid_constant__ CUtensorMap mOut, Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* bars = smem + NSTAGE * STAGE_BYTES;
+    float* obuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);  // 2 x [OG][TM]
+    uint8_t* bars = smem + NSTAGE * STAGE_BYTES + 2 * OUT_BYTES;
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NSTAGE, tfull0 = empty0 + 8 * NSTAGE,
                    tempty0 = tfull0 + 16, drain = tempty0 + 16;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 128);
@@ -273,11 +309,17 @@ __global__ void __launch_bounds__(256, 1)
         // ---------------------------------------------------------------- epilogue
         const int q = warp & 3;
         const int row = 32 * q + lane;
-        uint32_t j = 0;
+        const bool issuer = (warp == 4 && lane == 0);
+        uint32_t j = 0, box = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             const int mt = t % num_m, nt = t / num_m;
             const uint32_t acc = j & 1, aph = (j >> 1) & 1;
-            if (!mbar_wait(tfull0 + 8 * acc, aph, abort_flag, WAIT_LIMIT_NS)) break;
+            const bool ok = mbar_wait(tfull0 + 8 * acc, aph, abort_flag, WAIT_LIMIT_NS);
+            if (a.direct) {
+                if (!epi_all(ok)) break;
+            } else if (!ok) {
+                break;
+            }
             fence_after();
             const int col = mt * TM + row;
             const bool col_ok = col < a.M;
@@ -285,17 +327,30 @@ __global__ void __launch_bounds__(256, 1)
             for (int n0 = 0; n0 < TN; n0 += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + acc * TN + n0, r);
+                if (n0 + 32 == TN) {
+                    // the accumulator is in registers: the next tile's MMAs may start
+                    fence_before();
+                    mbar_arrive(tempty0 + 8 * acc);
+                }
                 const int g0 = nt * TN + n0;
                 if (a.direct) {
+                    if (g0 >= a.G) continue;  // block-uniform: whole box beyond the last glyph
+                    float* buf = obuf + (box & 1) * (OG * TM);
+                    if (issuer) bulk_wait_read1();  // the store issued two boxes ago has read `buf`
+                    epi_bar();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        const int g = g0 + i;
-                        if (g < a.G && col_ok) {
-                            float v = __uint_as_float(r[i]);
-                            if (ch == 0 && a.view.r0) v -= __ldg(a.view.r0 + g);
-                            a.out[(int64_t)g * a.M + col] = v;
-                        }
+                        float v = __uint_as_float(r[i]);
+                        if (ch == 0 && a.view.r0 && g0 + i < a.G) v -= __ldg(a.view.r0 + g0 + i);
+                        buf[i * TM + row] = v;
                     }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    epi_bar();
+                    if (issuer) {
+                        tma_store_2d(&mOut, smem_u32(buf), mt * TM, g0);  // clipped at M columns, G rows
+                        bulk_commit();
+                    }
+                    ++box;
                 } else {
                     // gather the four channels of a texel into the lane holding channel 0
                     const int P = a.view.N_uniform + 2;
@@ -316,9 +371,8 @@ __global__ void __launch_bounds__(256, 1)
                     }
                 }
             }
-            fence_before();
-            mbar_arrive(tempty0 + 8 * acc);
         }
+        if (issuer) bulk_wait_all();
     }
     __syncthreads();
     if (threadIdx.x == 0 && *abort_flag && a.dev_status) atomicOr(a.dev_status, SHM_DEV_TIMEOUT);
@@ -380,6 +434,21 @@ static bool make_map(CUtensorMap* m, const float* base, int rows, int Kp, int bo
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Output table as a 2-D tensor [G rows][M columns] f32 (row pitch M * 4 B, a multiple of 16 since
+// M = 4 * 6 (N+2)^2), stored in boxes of [OG glyphs][TM columns] without swizzle.
+static bool make_out_map(CUtensorMap* m, float* base, int G, int M)
+{
+    EncodeFn enc = encode_fn();
+    if (!enc || ((uintptr_t)base & 15u) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)G};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)TM, (cuuint32_t)OG};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace tc
 
 // K padded to a multiple of 32 (a multiple of the stage K; the layout is part of shm_sh_basis's contract)
@@ -413,10 +482,16 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     if (e != cudaSuccess) return e;
     const float* bhi = basis + (int64_t)K * M;
     const float* blo = bhi + (int64_t)M * Kp;
-    CUtensorMap mAh, mAl, mBh, mBl;
+    CUtensorMap mAh, mAl, mBh, mBl, mOut;
     if (!tc::make_map(&mAh, bhi, M, Kp, tc::TM) || !tc::make_map(&mAl, blo, M, Kp, tc::TM) ||
         !tc::make_map(&mBh, chi, G, Kp, tc::TN) || !tc::make_map(&mBl, clo, G, Kp, tc::TN))
         return cudaErrorInvalidValue;
+    const bool direct = (out.dtype == SHM_F32 && out.layout == SHM_LAYOUT_TEXEL);
+    if (direct) {
+        if (!tc::make_out_map(&mOut, reinterpret_cast<float*>(data), G, M)) return cudaErrorInvalidValue;
+    } else {
+        mOut = mAh;  // unused by the generic epilogue
+    }
     tc::Args a;
     a.M = M;
     a.G = G;
@@ -424,7 +499,7 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     a.view = out;
     a.data = data;
     a.out = reinterpret_cast<float*>(data);
-    a.direct = (out.dtype == SHM_F32 && out.layout == SHM_LAYOUT_TEXEL) ? 1 : 0;
+    a.direct = direct ? 1 : 0;
     a.dev_status = dev_status;
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -435,7 +510,7 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     const int tiles = ((M + tc::TM - 1) / tc::TM) * ((G + tc::TN - 1) / tc::TN);
     int grid = sm_count();
     if (grid > tiles) grid = tiles;
-    tc::k_sh_gemm_tc<<<grid, 256, tc::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, a);
+    tc::k_sh_gemm_tc<<<grid, 256, tc::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, mOut, a);
     return cudaGetLastError();
 }
 

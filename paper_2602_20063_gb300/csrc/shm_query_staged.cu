@@ -1,0 +1,208 @@
+// Staged query (§3.2-§3.4) for per-glyph query segments on tables that fit in shared memory.
+//
+// With CSR segments every glyph's queries are contiguous, so a CTA can take a whole glyph: one
+// bulk copy (cp.async.bulk, completion on an mbarrier) brings the glyph's padded table into shared
+// memory, then the CTA answers all of that glyph's queries from it.  The table is read from HBM
+// once, the 2x2 footprints become shared-memory reads, and HBM sees only the bulk copy and the
+// coalesced direction / output streams (for N = 32, f32: 111 KB + 4,096 x 40 B per glyph), instead
+// of texel reads that miss L1 about half of the time.  Two CTAs per SM overlap one CTA's copy with
+// the other's queries.
+//
+// Results are bit-identical to k_query_fwd (same device functions on the same values).
+// The wait for the copy is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, waits up to
+// 100 ms more for its copy to land and returns without touching the outputs of that glyph.
+#include "shm_internal.h"
+
+namespace shm {
+
+namespace {
+
+constexpr int SBLOCK = 512;
+constexpr uint64_t STAGE_WAIT_NS = 1000000000ull;   // 1 s
+constexpr uint64_t STAGE_DRAIN_NS = 100000000ull;   // 100 ms
+constexpr uint32_t BULK_PIECE = 32768;               // bytes per cp.async.bulk
+constexpr int TABLE_OFFSET = 128;                    // mbarrier first, table 128-byte aligned
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit)
+{
+    if (bar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!bar_try_wait(bar, parity))
+        if (gtimer() - t0 > limit) return false;
+    return true;
+}
+
+template <int DT>
+__device__ __forceinline__ float4 smem_rec(const unsigned char* table, int rec)
+{
+    if (DT == SHM_F32) return reinterpret_cast<const float4*>(table)[rec];
+    const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
+    return DT == SHM_F16 ? h4_to_f4(v) : b4_to_f4(v);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_t table_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem);
+    const unsigned char* table = smem + TABLE_OFFSET;
+    const uint32_t table_s = bar + TABLE_OFFSET;
+    const int tid = threadIdx.x;
+    const int G = a.L.n_glyphs, N = a.L.N_uniform, P = N + 2;
+    const float qnan = __int_as_float(0x7fc00000);
+    uint32_t status = 0;
+
+    // queries outside every segment: NaN and SHM_DEV_BOUNDS, as in the unstaged kernel
+    {
+        const int64_t lo = min(max(__ldg(a.seg), (int64_t)0), a.Q);
+        const int64_t hi = min(max(__ldg(a.seg + G), lo), a.Q);
+        const int64_t stride = (int64_t)gridDim.x * SBLOCK;
+        for (int part = 0; part < 2; ++part) {
+            const int64_t b = part ? hi : 0, e = part ? a.Q : lo;
+            for (int64_t q = b + (int64_t)blockIdx.x * SBLOCK + tid; q < e; q += stride) {
+                status |= SHM_DEV_BOUNDS;
+                if (a.R) a.R[q] = qnan;
+                if (a.grad) { a.grad[3 * q] = qnan; a.grad[3 * q + 1] = qnan; a.grad[3 * q + 2] = qnan; }
+                if (a.normal) { a.normal[3 * q] = qnan; a.normal[3 * q + 1] = qnan; a.normal[3 * q + 2] = qnan; }
+                if (a.chart) { a.chart[2 * q] = qnan; a.chart[2 * q + 1] = qnan; }
+                if (a.fij) { a.fij[3 * q] = -1; a.fij[3 * q + 1] = -1; a.fij[3 * q + 2] = -1; }
+            }
+        }
+    }
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const int64_t s0 = min(max(__ldg(a.seg + g), (int64_t)0), a.Q);
+        const int64_t s1 = min(max(__ldg(a.seg + g + 1), s0), a.Q);
+        if (s1 <= s0) continue;  // block-uniform
+        if (tid == 0) {
+            // the previous glyph's table was read through the generic proxy: order those reads
+            // before the async-proxy writes of the copy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(table_bytes)
+                         : "memory");
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(a.L.data) +
+                                       (size_t)g * (size_t)table_bytes;
+            for (uint32_t off = 0; off < table_bytes; off += BULK_PIECE) {
+                const uint32_t n = min(BULK_PIECE, table_bytes - off);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    ::"r"(table_s + off), "l"(src + off), "r"(n), "r"(bar)
+                    : "memory");
+            }
+        }
+        // first direction of this thread while the copy runs
+        int64_t q = s0 + tid;
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        if (q < s1) { d0 = __ldg(a.dirs + 3 * q); d1 = __ldg(a.dirs + 3 * q + 1); d2 = __ldg(a.dirs + 3 * q + 2); }
+        if (!bar_wait(bar, phase, STAGE_WAIT_NS)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            status |= SHM_DEV_TIMEOUT;
+            if (tid == 0) bar_wait(bar, phase, STAGE_DRAIN_NS);
+            break;
+        }
+        phase ^= 1;
+        const float r0 = a.L.r0 ? __ldg(a.L.r0 + g) : 0.0f;
+        for (; q < s1; q += SBLOCK) {
+            const int64_t qn = q + SBLOCK;
+            float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+            if (qn < s1) { n0 = __ldg(a.dirs + 3 * qn); n1 = __ldg(a.dirs + 3 * qn + 1); n2 = __ldg(a.dirs + 3 * qn + 2); }
+            Chart c;
+            float R = qnan, Ru = qnan, Rv = qnan;
+            Vec3 grad{qnan, qnan, qnan}, nrm{qnan, qnan, qnan};
+            int f = -1, i = -1, j = -1;
+            if (chart_of(d0, d1, d2, c)) {
+                float s, t;
+                cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, N, i, s);
+                cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, N, j, t);
+                const int rec = (c.f * P + j) * P + i;
+                Corners cr;
+                cr.c00 = smem_rec<DT>(table, rec);
+                cr.c10 = smem_rec<DT>(table, rec + 1);
+                cr.c01 = smem_rec<DT>(table, rec + P);
+                cr.c11 = smem_rec<DT>(table, rec + P + 1);
+                const HermOut h = hermite2(cr, s, t);
+                R = r0 + h.r;
+                Ru = (float)N * h.rs;
+                Rv = (float)N * h.rt;
+                grad = s2_gradient(c, Ru, Rv);
+                if (a.normal) nrm = surface_normal(d0, d1, d2, R, grad);
+                f = c.f;
+            } else {
+                status |= SHM_DEV_NONFINITE;
+            }
+            if (a.R) a.R[q] = R;
+            if (a.grad) { a.grad[3 * q] = grad.x; a.grad[3 * q + 1] = grad.y; a.grad[3 * q + 2] = grad.z; }
+            if (a.normal) { a.normal[3 * q] = nrm.x; a.normal[3 * q + 1] = nrm.y; a.normal[3 * q + 2] = nrm.z; }
+            if (a.chart) { a.chart[2 * q] = Ru; a.chart[2 * q + 1] = Rv; }
+            if (a.fij) { a.fij[3 * q] = f; a.fij[3 * q + 1] = i; a.fij[3 * q + 2] = j; }
+            d0 = n0; d1 = n1; d2 = n2;
+        }
+        __syncthreads();  // every read of this table is done before the next copy lands
+    }
+    report_status(a.dev_status, status);
+}
+
+template <int DT>
+cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
+{
+    const int smem = TABLE_OFFSET + (int)table_bytes;
+    static int configured = -1;
+    if (configured != smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_query_staged<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int resident = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT>, SBLOCK, smem) != cudaSuccess ||
+        resident < 1)
+        resident = 1;
+    int64_t blocks = (int64_t)sm_count() * resident;
+    if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
+    if (blocks < 1) blocks = 1;
+    k_query_staged<DT><<<(unsigned)blocks, SBLOCK, smem, s>>>(a, table_bytes);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_query_staged(const QueryArgs& a, cudaStream_t s)
+{
+    const int64_t P = (int64_t)a.L.N_uniform + 2;
+    const int64_t rb = (a.L.dtype == SHM_F32) ? 16 : 8;
+    const uint32_t table_bytes = (uint32_t)(6 * P * P * rb);
+    if (a.L.dtype == SHM_F32) return launch_staged_t<SHM_F32>(a, table_bytes, s);
+    if (a.L.dtype == SHM_F16) return launch_staged_t<SHM_F16>(a, table_bytes, s);
+    return launch_staged_t<SHM_BF16>(a, table_bytes, s);
+}
+
+}  // namespace shm

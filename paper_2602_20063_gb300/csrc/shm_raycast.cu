@@ -142,6 +142,30 @@ __device__ __forceinline__ bool surface_F(const LutView& L, const GlyphRef& G, f
     return true;
 }
 
+// Refinement steps of one object by its projected radius (see shm_raycast_params).  The radius
+// decides integers, so it is formed with round-to-nearest intrinsics (no contraction into FMA),
+// operation by operation as written.
+__device__ __forceinline__ void lod_steps(const shm_raycast_params& prm, const shm_camera& cam, const shm_object& ob,
+                                          int& bisect, int& newton)
+{
+    bisect = prm.bisect;
+    newton = prm.newton;
+    if (!prm.lod) return;
+    const float dx = __fsub_rn(ob.centre[0], cam.eye[0]);
+    const float dy = __fsub_rn(ob.centre[1], cam.eye[1]);
+    const float dz = __fsub_rn(ob.centre[2], cam.eye[2]);
+    const float D = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+    const float p = __fdiv_rn(__fmul_rn(ob.rmax, 0.5f * (float)cam.H), __fmul_rn(D, cam.tan_half_fov_y));
+    const float need = 128.0f * p;
+    for (int b = prm.bisect_min; b <= prm.bisect; ++b) {
+        if ((float)prm.march * __int_as_float((127 + b) << 23) >= need) {  // march * 2^b, exact
+            bisect = b;
+            break;
+        }
+    }
+    newton = (p >= 64.0f) ? prm.newton : prm.newton_min;
+}
+
 template <int DT, int LAYOUT>
 __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object* __restrict__ objs, int n, shm_camera cam,
                                                     shm_raycast_params prm, const int32_t* __restrict__ counts,
@@ -197,6 +221,8 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
             if (t1 <= 0.0f) continue;
             if (t0 < 0.0f) t0 = 0.0f;
             if (t0 >= best_t) continue;
+            int n_bisect, n_newton;
+            lod_steps(prm, cam, ob, n_bisect, n_newton);
             const GlyphRef G = glyph_ref(L, ob.glyph);
             Surf S;
             float thit = qnan;
@@ -219,14 +245,14 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
                     }
                 }
                 if (!found) continue;
-                for (int it = 0; it < prm.bisect; ++it) {
+                for (int it = 0; it < n_bisect; ++it) {
                     const float mid = 0.5f * (lo + hi);
                     surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, mid, S);
                     ++nq;
                     if (S.F < 0.0f) hi = mid; else lo = mid;
                 }
                 float t = 0.5f * (lo + hi);
-                for (int it = 0; it < prm.newton; ++it) {
+                for (int it = 0; it < n_newton; ++it) {
                     surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t, S);
                     ++nq;
                     if (S.dF == 0.0f) break;

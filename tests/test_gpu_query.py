@@ -178,3 +178,57 @@ def test_vector_and_scalar_io_paths_agree(S, layout):
     b = S.query(L, d_un, want=("R", "grad", "normal", "chart", "fij"))
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+def _same(a, b):
+    return bool(((a == b) | (torch.isnan(a) & torch.isnan(b))).all())
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+def test_staged_segments_match_unstaged(S, dtype):
+    """Per-glyph segments on a small uniform table take the shared-memory staged kernel; glyph ids
+    on the same queries take the unstaged one.  Identical results, including queries outside every
+    segment (NaN + SHM_DEV_BOUNDS), empty segments and ragged segment lengths."""
+    G, N = 9, 20
+    luts = [O.bake_sh(N, 6, I.sh_coeffs(1, 6, 500 + g)[0]) for g in range(G)]
+    r0 = np.linspace(-0.3, 0.6, G).astype(np.float32)
+    L, stored = upload_pool(S, luts, r0=r0, dtype=dtype)
+    counts = np.array([1000, 0, 17, 4096, 513, 0, 1, 2047, 300])
+    pre, post = 37, 11
+    Q = pre + int(counts.sum()) + post
+    dirs = I.directions(Q, 501)
+    dirs[pre + 5] = 0.0                      # one invalid direction inside a segment
+    seg = np.concatenate([[pre], pre + np.cumsum(counts)]).astype(np.int64)
+    glyph = np.full(Q, -1, np.int32)
+    for g in range(G):
+        glyph[seg[g]:seg[g + 1]] = g
+    d = torch.from_numpy(dirs).cuda()
+    want = ("R", "grad", "normal", "chart", "fij")
+    st1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a = S.query(L, d, seg=torch.from_numpy(seg).cuda(), want=want, dev_status=st1)
+    b = S.query(L, d, glyph=torch.from_numpy(glyph).cuda(), want=want, dev_status=st2)
+    for k in want:
+        assert _same(a[k], b[k]), k
+    assert st1.item() == st2.item() == (S.SHM_DEV_BOUNDS | S.SHM_DEV_NONFINITE)
+    # and against the oracle on the covered queries
+    off, Ns = O.make_pool(luts)[1:]
+    cov = glyph >= 0
+    cov[pre + 5] = False
+    ref = O.query(stored.reshape(-1, 4), off, Ns, dirs[cov], glyph=glyph[cov], r0=r0.astype(np.float64))
+    check_query({k: v[torch.from_numpy(cov).cuda()] for k, v in a.items() if k in ("R", "grad", "normal")}, ref)
+
+
+def test_staged_glyph_field_size(S):
+    """The glyph-field shape (N = 32, f32: 111 KB tables, two CTAs per SM), 512 glyphs."""
+    G, N, per = 512, 32, 1024
+    coeffs = I.sh_coeffs(G, 8, 510).astype(np.float32)
+    lut = S.alloc_lut(G, N)
+    S.build_lut(lut, S.Source(kind=S.SHM_SRC_SH, L=8, coeffs=torch.from_numpy(coeffs).cuda(), basis=S.sh_basis(N, 8)))
+    dirs = torch.from_numpy(I.directions(G * per, 511)).cuda()
+    seg = torch.from_numpy(I.query_glyphs_csr(G, per)).cuda()
+    glyph = torch.from_numpy(np.repeat(np.arange(G, dtype=np.int32), per)).cuda()
+    a = S.query(lut, dirs, seg=seg, want=("R", "grad", "normal", "fij"))
+    b = S.query(lut, dirs, glyph=glyph, want=("R", "grad", "normal", "fij"))
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
