@@ -227,20 +227,48 @@ class GlyphField:
         return self.Q
 
     def e2e_step(self, host_out):
-        """Public API from pinned host buffers: H2D directions + coefficients, bake, query, D2H outputs."""
-        self.dirs.copy_(self.dirs_host, non_blocking=True)
-        self.coeffs.copy_(self.c_pinned, non_blocking=True)
-        self.S.build_lut(self.lut, self.src, ws=self.ws)
-        self.S.query(self.lut, self.dirs, seg=self.seg, out=self.out)
-        for k in ("R", "grad", "normal"):
-            host_out[k].copy_(self.out[k], non_blocking=True)
+        """Public API from pinned host buffers, pipelined over glyph chunks on two streams: per chunk
+        H2D of its directions and coefficients, bake, query, D2H of its outputs, so that the copy
+        engines and the kernels of neighbouring chunks overlap."""
+        torch, S = self.torch, self.S
+        main = torch.cuda.current_stream()
+        for st in self.e2e_streams:
+            st.wait_stream(main)
+        for c, (lut_c, src_c, seg_c, g0, g1) in enumerate(self.e2e_chunks):
+            st = self.e2e_streams[c % 2]
+            q0, q1 = g0 * self.per, g1 * self.per
+            with torch.cuda.stream(st):
+                self.dirs[q0:q1].copy_(self.dirs_host[q0:q1], non_blocking=True)
+                self.coeffs[g0:g1].copy_(self.c_pinned[g0:g1], non_blocking=True)
+                S.build_lut(lut_c, src_c, ws=self.e2e_ws[c % 2], stream=st)
+                out_c = {k: v[q0:q1] for k, v in self.out.items()}
+                S.query(lut_c, self.dirs[q0:q1], seg=seg_c, out=out_c, stream=st)
+                for k in ("R", "grad", "normal"):
+                    host_out[k][q0:q1].copy_(out_c[k], non_blocking=True)
+        for st in self.e2e_streams:
+            main.wait_stream(st)
 
-    def e2e_setup(self):
-        torch = self.torch
+    def e2e_setup(self, chunks=8):
+        torch, S = self.torch, self.S
         self.c_pinned = torch.from_numpy(self.c_host).pin_memory()
         host_out = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in self.out.items()}
         h2d = self.dirs.numel() * 4 + self.coeffs.numel() * 4
         d2h = sum(v.numel() * 4 for v in self.out.values())
+        self.e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        per_glyph = S.records_per_glyph(self.N, self.layout) * S.record_bytes(self.dtype, self.layout)
+        elem = self.lut.data.element_size()
+        self.e2e_chunks = []
+        Gc = (self.G + chunks - 1) // chunks
+        for g0 in range(0, self.G, Gc):
+            g1 = min(self.G, g0 + Gc)
+            lut_c = S.Lut(data=self.lut.data[g0 * per_glyph // elem:g1 * per_glyph // elem], n_glyphs=g1 - g0,
+                          dtype=self.dtype, layout=self.layout, N_uniform=self.N)
+            src_c = S.Source(kind=S.SHM_SRC_SH, L=self.L, coeffs=self.coeffs[g0:g1], basis=self.basis)
+            seg_c = (self.seg[g0:g1 + 1] - self.seg[g0]).contiguous()
+            self.e2e_chunks.append((lut_c, src_c, seg_c, g0, g1))
+        ws_c = self.e2e_chunks[0][1]
+        self.e2e_ws = ([S.build_workspace(self.e2e_chunks[0][0], ws_c) for _ in range(2)]
+                       if self.engine == "tcgen05" else [None, None])
         return host_out, h2d, d2h
 
     def roofline_terms(self, peaks, kernel_ms, sms):
@@ -515,6 +543,24 @@ class Planet:
                         "max_err_grad_rel_vs_f32": float((o["grad"] - ref["grad"]).abs().max()
                                                          / ref["grad"].norm(dim=1).max())}
             del L2, o
+        # random-gather ceiling: the same traffic pattern (12 B in, one aligned block gathered from a
+        # table of the planet's size, 28 B out) without the arithmetic
+        probe_out = torch.empty((self.Qr, 7), dtype=torch.float32, device="cuda")
+        ceiling = {}
+        for blk, tab_name in ((64, "f32_cell"), (32, "f16_cell")):
+            Lc = S.like_lut(base, dtype=0 if blk == 64 else 1, layout=1)
+            ms = timeit(lambda: S.gather_probe(Lc.data, blk, self.dr, out=probe_out))
+            q_ms = ex[tab_name]["query_random_ms"]
+            ceiling[f"{blk}B"] = {"probe_ms": round(ms, 4), "items_per_s": self.Qr / (ms * 1e-3),
+                                  "GBps_at_block_plus_40B": (blk + 40) * self.Qr / (ms * 1e-3) / 1e9,
+                                  "frac_of_measured_hbm": round((blk + 40) * self.Qr / (ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"], 3),
+                                  f"query_{tab_name}_over_probe_time": round(q_ms / ms, 3)}
+            del Lc
+        ceiling["note"] = ("uncorrelated 64 B / 32 B gathers from the matching cell-layout table (1.61 GB f32 / "
+                           "0.81 GB f16: 4 corner records per cell), per item 12 B read + 28 B written; the query on "
+                           "that layout does the same traffic plus the chart, Hermite and S^2 arithmetic")
+        ex["random_gather_ceiling"] = ceiling
+        del probe_out
         # derivative-consistent mip chain (§4.7) of the f32 texel table: 2048 -> 1024 -> ... -> 16
         chain = [base]
         for _ in range(7):

@@ -335,6 +335,16 @@ shm_status shm_raycast_noalloc(const shm_lut* lut, const shm_object* objs, int32
                                float* depth, float* normal, int32_t* obj_id, int32_t* dev_status,
                                shm_stream stream);
 
+/* ---------------------------------------------------------------- measurement aid (not in the paper) */
+
+/* Random-gather ceiling: the memory traffic of an uncorrelated query batch without its
+ * arithmetic, to measure what the memory system sustains for that access pattern.  For each
+ * q < Q: reads in[3q..3q+2] (12 B), gathers one block_bytes block (16, 32, 48 or 64; 16-byte
+ * aligned `table` of table_bytes) at a position hashed from those three values, writes
+ * out[7q..7q+6] (28 B).  The values written are meaningless. */
+shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t block_bytes, int64_t Q,
+                            const float* in, float* out, shm_stream stream);
+
 /* ---------------------------------------------------------------- misc */
 
 const char* shm_status_string(shm_status s);

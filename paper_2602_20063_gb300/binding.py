@@ -84,6 +84,7 @@ _SIGS = {
     "shm_raycast_workspace_bytes": (C.c_int64, [_I32, _I32, _I32]),
     "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "shm_raycast_noalloc": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_gather_probe": (C.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP]),
     "shm_status_string": (C.c_char_p, [C.c_int]),
     "shm_version": (C.c_int32, []),
 }
@@ -507,3 +508,16 @@ def raycast_noalloc(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm
 def raycast_query_count(ws: torch.Tensor) -> int:
     """Surface queries the last shm_raycast on this workspace evaluated (workspace header)."""
     return int(ws[8:16].view(torch.int64).item())
+
+
+# ------------------------------------------------------------------------------------------- measurement aid
+def gather_probe(table: torch.Tensor, block_bytes: int, inp: torch.Tensor, out: torch.Tensor = None, stream=None):
+    """shm_gather_probe: the random-gather traffic of a query batch (12 B in, one block gathered,
+    28 B out per item) without the arithmetic."""
+    _need(inp, torch.float32, name="in")
+    Q = inp.shape[0]
+    if out is None:
+        out = torch.empty((Q, 7), dtype=torch.float32, device=inp.device)
+    _check(lib().shm_gather_probe(_ptr(table), table.numel() * table.element_size(), int(block_bytes), Q, _ptr(inp),
+                                  _ptr(out), _stream(stream)), "shm_gather_probe")
+    return out

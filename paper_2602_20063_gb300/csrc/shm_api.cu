@@ -159,6 +159,16 @@ shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const 
     return map_cuda(launch_query_recon(a, method, (cudaStream_t)stream));
 }
 
+shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t block_bytes, int64_t Q, const float* in,
+                            float* out, shm_stream stream)
+{
+    if (!table || Q < 0 || (Q > 0 && (!in || !out))) return SHM_ERR_INVALID_ARG;
+    if (block_bytes < 16 || block_bytes > 64 || block_bytes % 16 != 0 || ((uintptr_t)table & 15u) != 0 ||
+        table_bytes < block_bytes)
+        return SHM_ERR_INVALID_ARG;
+    return map_cuda(launch_gather_probe(table, table_bytes, block_bytes, Q, in, out, (cudaStream_t)stream));
+}
+
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
 {
     if (N < 1 || L < 0 || L > 20) return -1;

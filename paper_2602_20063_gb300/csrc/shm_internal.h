@@ -131,6 +131,8 @@ cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s);
 // of 512 threads per SM: (232,448 - 2 x 1 KB reserved) / 2 minus the barrier block).
 constexpr int64_t STAGED_TABLE_MAX_BYTES = 114688;
 cudaError_t launch_query_staged(const QueryArgs& a, cudaStream_t s);
+cudaError_t launch_gather_probe(const void* table, int64_t table_bytes, int block_bytes, int64_t Q, const float* in,
+                                float* out, cudaStream_t s);
 cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s);
 cudaError_t launch_adam(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
                         float eps, int step, int zero_grad, cudaStream_t s);

@@ -101,3 +101,46 @@ def test_build_backward(S, N, L, G):
     for g in range(min(G, 6)):
         ref = O.bake_sh_vjp(N, L, dlut[g].astype(np.float64).reshape(6, N + 2, N + 2, 4))
         assert np.abs(dc[g] - ref).max() <= 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_segments_and_glyph_ids_agree_with_oracle(S, dtype):
+    """The reverse pass with CSR segments and with glyph ids on the same queries, both against the
+    oracle, accumulating into a non-zero dL/dtable, with queries outside every segment (NaN
+    direction gradients, SHM_DEV_BOUNDS) and an empty segment."""
+    G, N = 7, 14
+    luts = [O.bake_sh(N, 5, I.sh_coeffs(1, 5, 600 + g)[0] + np.eye(1, 36, 0)[0] * 2.0) for g in range(G)]
+    r0 = np.linspace(0.0, 0.4, G).astype(np.float32)
+    L, stored = upload_pool(S, luts, r0=r0, dtype=dtype)
+    counts = np.array([700, 0, 4096, 33, 1500, 2, 999])
+    pre, post = 5, 9
+    Q = pre + int(counts.sum()) + post
+    dirs = I.directions(Q, 601)
+    seg = np.concatenate([[pre], pre + np.cumsum(counts)]).astype(np.int64)
+    glyph = np.full(Q, -1, np.int32)
+    for g in range(G):
+        glyph[seg[g]:seg[g + 1]] = g
+    rng = np.random.default_rng(602)
+    gR = rng.normal(size=Q).astype(np.float32)
+    gG = rng.normal(size=(Q, 3)).astype(np.float32)
+    gn = rng.normal(size=(Q, 3)).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    init = torch.from_numpy(rng.normal(size=G * 6 * (N + 2) ** 2 * 4).astype(np.float32)).cuda()
+    dl_s, dl_u = S.like_lut(L, dtype=0, layout=0), S.like_lut(L, dtype=0, layout=0)
+    dl_s.data.copy_(init)
+    dl_u.data.copy_(init)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dd_s = S.query_backward(L, t(dirs), dl_s, gR=t(gR), ggrad=t(gG), gnormal=t(gn), seg=t(seg), dev_status=st)
+    dd_u = S.query_backward(L, t(dirs), dl_u, gR=t(gR), ggrad=t(gG), gnormal=t(gn), glyph=t(glyph))
+    assert st.item() & S.SHM_DEV_BOUNDS
+    both_nan = torch.isnan(dd_s) & torch.isnan(dd_u)
+    assert bool(((dd_s == dd_u) | both_nan).all())          # per-query, no accumulation order involved
+    cov = glyph >= 0
+    off, Ns = O.make_pool(luts)[1:]
+    dref, _ = O.query_vjp(stored.reshape(-1, 4), off, Ns, dirs[cov], gR=gR[cov], gG=gG[cov], gn=gn[cov],
+                          glyph=glyph[cov], r0=r0.astype(np.float64), want_ddirs=False)
+    base = init.double().cpu().numpy().reshape(-1, 4)
+    for dl in (dl_s, dl_u):
+        got = dl.data.view(-1, 4).double().cpu().numpy() - base
+        for ch in range(4):
+            assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * np.abs(dref[:, ch]).max() + 4e-7 * np.abs(base[:, ch]).max(), ch

@@ -124,3 +124,20 @@ def test_short_fit_reduces_loss(S):
         S.adam_step(lut.data, dl.data, m, v, lr=1e-2, step=step)
         losses.append(loss.item() / (G * per))
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+def test_adam_vector_and_scalar_paths_agree(S):
+    """16-byte aligned arrays take 128-bit accesses (with a scalar tail), offset views the scalar
+    path; element results are identical."""
+    rng = np.random.default_rng(90)
+    n = 4099
+    base = [rng.normal(size=n + 1).astype(np.float32) for _ in range(4)]
+    base[3] = np.abs(base[3])
+    A = [torch.from_numpy(b[:n].copy()).cuda() for b in base]          # aligned
+    B = [torch.from_numpy(b.copy()).cuda()[1:] for b in base]          # 4-byte offset views
+    for b, a in zip(B, A):
+        b.copy_(a)
+    S.adam_step(A[0], A[1], A[2], A[3], lr=1e-2, step=3, zero_grad=True)
+    S.adam_step(B[0], B[1], B[2], B[3], lr=1e-2, step=3, zero_grad=True)
+    for a, b in zip(A, B):
+        assert torch.equal(a, b)
