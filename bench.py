@@ -177,6 +177,13 @@ def load_traffic(kernel, files):
 
 
 # ----------------------------------------------------------------------------------- workloads
+class _NoTimer:
+    """Stand-in for KernelTimer when a step runs outside the timed region."""
+
+    def mark(self, name):
+        pass
+
+
 class GlyphField:
     name = "glyphs"
     unit = "queries/s"
@@ -340,7 +347,24 @@ class GlyphField:
             del L16, o16
         del dl
         ex["recon"] = self.recon_extras(S, torch, timeit, n, fwd)
+        ex["cuda_graph"] = self.graph_extras(S, torch, timeit, n)
         return ex
+
+    def graph_extras(self, S, torch, timeit, n):
+        """The step (bake + query) captured once in a CUDA graph and replayed, against eager launches."""
+        eager = timeit(lambda: self.step(_NoTimer()), n)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.step(_NoTimer())  # warm the capture stream
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(graph):
+            self.step(_NoTimer())
+        replay = timeit(graph.replay, n)
+        return {"eager_ms": round(eager, 4), "graph_replay_ms": round(replay, 4),
+                "queries_per_s_graph": self.Q / (replay * 1e-3),
+                "launches_per_step": self.launches_per_step}
 
     def recon_extras(self, S, torch, timeit, n, hermite_ms):
         """Value-only baselines (§4.2, §4.5) on the same glyphs, directions and segments: a value

@@ -12,10 +12,12 @@
 //   chart   x = d_k1/|d_k|, y = d_k2/|d_k|, s = (x+1)N/2 + 1/2 - i:  gd from gx + gs N/2, gy + gt N/2
 //   w = d/|d|                               gd += (gw - w (w.gw))/|d|
 // Face and cell indices are piecewise constant, so they carry no derivative.
-// (A variant that accumulated each glyph's gradients in a shared-memory slab with shared float
-// atomics measured 4.8 ms against 3.3 ms for the global vector atomics on the 2^26-query glyph
-// field: sixteen scattered 4-byte shared atomics per query cost more than four 16-byte L2 ones.)
-#include "shm_internal.h"
+// Per-glyph segments on small uniform tables take k_query_bwd_staged: the table is staged in shared
+// memory as in the forward.  (Accumulating each glyph's gradients in a shared-memory slab with
+// shared float atomics instead measured 4.8 ms against 3.3 ms for the global vector atomics on the
+// 2^26-query glyph field: sixteen scattered 4-byte shared atomics per query cost more than four
+// 16-byte L2 ones.)
+#include "shm_stage.cuh"
 
 namespace shm {
 
@@ -42,18 +44,20 @@ __device__ __forceinline__ Herm2 herm2(float s)
     return h;
 }
 
-// One query's reverse pass on glyph table Gr: corner-record gradients go to `sink(record, float4)`
-// (record index within the glyph's texel table), the direction gradient to dd.
-template <int DT, int LAYOUT, bool FIT, class Sink>
+// One query's reverse pass on glyph table Gr: the 2x2 footprint comes from `fetch(f, i, j)`,
+// corner-record gradients go to `sink(record, float4)` (record index within the glyph's texel
+// table), the direction gradient to dd.
+template <bool FIT, class Fetch, class Sink>
 __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, const GlyphRef& Gr, const Chart& c,
-                                          float d0, float d1, float d2, Sink& sink, float3& dd, float& loss_acc)
+                                          float d0, float d1, float d2, const Fetch& fetch, Sink& sink, float3& dd,
+                                          float& loss_acc)
 {
     const int N = Gr.N;
     int i, j;
     float s, t;
     cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, N, i, s);
     cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, N, j, t);
-    const Corners cr = fetch_corners<DT, LAYOUT>(a.L.data, Gr, c.f, i, j);
+    const Corners cr = fetch(c.f, i, j);
     const Herm2 A = herm2(s), B = herm2(t);
     // --- forward (difference form) with second derivatives
     const float d0r = cr.c10.x - cr.c00.x, d1r = cr.c11.x - cr.c01.x;
@@ -176,7 +180,7 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
 }
 
 template <int DT, int LAYOUT, bool FIT>
-__global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
+__global__ void __launch_bounds__(BBLOCK, 3) k_query_bwd(BackwardArgs a)
 {
     float loss_acc = 0.0f;
     const int lane = threadIdx.x & 31;
@@ -217,7 +221,8 @@ __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
                 const GlyphRef Gd = glyph_ref(a.D, gq);
                 float4* dbase = reinterpret_cast<float4*>(a.dlut) + Gd.base;
                 auto sink = [dbase](int rec, float4 wv) { atomicAdd(dbase + rec, wv); };
-                bwd_query<DT, LAYOUT, FIT>(a, q, Gr, c, d0, d1, d2, sink, dd, loss_acc);
+                auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
+                bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
             }
             if (a.ddirs) {
                 a.ddirs[3 * q] = dd.x;
@@ -231,6 +236,100 @@ __global__ void __launch_bounds__(BBLOCK) k_query_bwd(BackwardArgs a)
         if ((threadIdx.x & 31) == 0 && a.loss) atomicAdd(a.loss, loss_acc);
     }
     report_status(a.dev_status, status);
+}
+
+// Per-glyph segments on tables that fit in shared memory: one CTA per glyph stages the table (as
+// the forward does) and answers the footprint reads from it; the gradient atomics of a glyph then
+// all come from one SM within a short window, so its dL/dtable slab stays in L2 while it is hit.
+constexpr int SBB = 512;
+
+template <int DT, bool FIT>
+__global__ void __launch_bounds__(SBB, 2) k_query_bwd_staged(BackwardArgs a, uint32_t table_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem);
+    const unsigned char* table = smem + stage::TABLE_OFFSET;
+    const int tid = threadIdx.x;
+    const int G = a.L.n_glyphs, N = a.L.N_uniform, P = N + 2;
+    uint32_t status = 0;
+    float loss_acc = 0.0f;
+    const float qnan = __int_as_float(0x7fc00000);
+    {
+        const int64_t lo = min(max(__ldg(a.seg), (int64_t)0), a.Q);
+        const int64_t hi = min(max(__ldg(a.seg + G), lo), a.Q);
+        const int64_t stride = (int64_t)gridDim.x * SBB;
+        for (int part = 0; part < 2; ++part) {
+            const int64_t b = part ? hi : 0, e = part ? a.Q : lo;
+            for (int64_t q = b + (int64_t)blockIdx.x * SBB + tid; q < e; q += stride) {
+                status |= SHM_DEV_BOUNDS;
+                if (a.ddirs) { a.ddirs[3 * q] = qnan; a.ddirs[3 * q + 1] = qnan; a.ddirs[3 * q + 2] = qnan; }
+            }
+        }
+    }
+    if (tid == 0) {
+        stage::init(bar);
+        s_abort = 0;
+    }
+    __syncthreads();
+    auto fetch = [table, P](int f, int i, int j) { return stage::corners<DT>(table, P, f, i, j); };
+    uint32_t phase = 0;
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const int64_t s0 = min(max(__ldg(a.seg + g), (int64_t)0), a.Q);
+        const int64_t s1 = min(max(__ldg(a.seg + g + 1), s0), a.Q);
+        if (s1 <= s0) continue;  // block-uniform
+        if (tid == 0)
+            stage::issue(bar, bar + stage::TABLE_OFFSET,
+                         reinterpret_cast<const unsigned char*>(a.L.data) + (size_t)g * table_bytes, table_bytes);
+        if (!stage::bar_wait(bar, phase, stage::WAIT_NS)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            status |= SHM_DEV_TIMEOUT;
+            if (tid == 0) stage::bar_wait(bar, phase, stage::DRAIN_NS);
+            break;
+        }
+        phase ^= 1;
+        const GlyphRef Gr = glyph_ref(a.L, g);
+        float4* dbase = reinterpret_cast<float4*>(a.dlut) + glyph_ref(a.D, g).base;
+        auto sink = [dbase](int rec, float4 wv) { atomicAdd(dbase + rec, wv); };
+        for (int64_t q = s0 + tid; q < s1; q += SBB) {
+            float3 dd = make_float3(qnan, qnan, qnan);
+            const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
+            Chart c;
+            if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+            else status |= SHM_DEV_NONFINITE;
+            if (a.ddirs) { a.ddirs[3 * q] = dd.x; a.ddirs[3 * q + 1] = dd.y; a.ddirs[3 * q + 2] = dd.z; }
+        }
+        __syncthreads();  // every read of this table is done before the next copy lands
+    }
+    if (FIT) {
+        for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+        if ((tid & 31) == 0 && a.loss) atomicAdd(a.loss, loss_acc);
+    }
+    report_status(a.dev_status, status);
+}
+
+template <int DT, bool FIT>
+static cudaError_t launch_bwd_staged_ft(const BackwardArgs& a, uint32_t table_bytes, cudaStream_t s)
+{
+    const int smem = stage::TABLE_OFFSET + (int)table_bytes;
+    static int configured = -1;
+    if (configured != smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_staged<DT, FIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int64_t blocks = (int64_t)sm_count() * 2;
+    if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
+    k_query_bwd_staged<DT, FIT><<<(unsigned)blocks, SBB, smem, s>>>(a, table_bytes);
+    return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t launch_bwd_staged(const BackwardArgs& a, uint32_t table_bytes, cudaStream_t s)
+{
+    return a.fit ? launch_bwd_staged_ft<DT, true>(a, table_bytes, s) : launch_bwd_staged_ft<DT, false>(a, table_bytes, s);
 }
 
 template <int DT, int LAYOUT>
@@ -250,6 +349,16 @@ cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s)
 {
     if (a.Q == 0) return cudaSuccess;
     const int dt = a.L.dtype, ly = a.L.layout;
+    // per-glyph segments on small uniform tables: stage each glyph's table in shared memory
+    if (a.seg && !a.glyph && a.L.N_uniform > 0 && a.D.N_uniform == a.L.N_uniform && ly == SHM_LAYOUT_TEXEL) {
+        const int64_t P = (int64_t)a.L.N_uniform + 2;
+        const int64_t bytes = 6 * P * P * (dt == SHM_F32 ? 16 : 8);
+        if (bytes <= STAGED_TABLE_MAX_BYTES) {
+            if (dt == SHM_F32) return launch_bwd_staged<SHM_F32>(a, (uint32_t)bytes, s);
+            if (dt == SHM_F16) return launch_bwd_staged<SHM_F16>(a, (uint32_t)bytes, s);
+            return launch_bwd_staged<SHM_BF16>(a, (uint32_t)bytes, s);
+        }
+    }
     if (ly == SHM_LAYOUT_TEXEL) {
         if (dt == SHM_F32) return launch_bwd_t<SHM_F32, SHM_LAYOUT_TEXEL>(a, s);
         if (dt == SHM_F16) return launch_bwd_t<SHM_F16, SHM_LAYOUT_TEXEL>(a, s);

@@ -11,54 +11,13 @@
 // Results are bit-identical to k_query_fwd (same device functions on the same values).
 // The wait for the copy is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, waits up to
 // 100 ms more for its copy to land and returns without touching the outputs of that glyph.
-#include "shm_internal.h"
+#include "shm_stage.cuh"
 
 namespace shm {
 
 namespace {
 
 constexpr int SBLOCK = 512;
-constexpr uint64_t STAGE_WAIT_NS = 1000000000ull;   // 1 s
-constexpr uint64_t STAGE_DRAIN_NS = 100000000ull;   // 100 ms
-constexpr uint32_t BULK_PIECE = 32768;               // bytes per cp.async.bulk
-constexpr int TABLE_OFFSET = 128;                    // mbarrier first, table 128-byte aligned
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint64_t limit)
-{
-    if (bar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (!bar_try_wait(bar, parity))
-        if (gtimer() - t0 > limit) return false;
-    return true;
-}
-
-template <int DT>
-__device__ __forceinline__ float4 smem_rec(const unsigned char* table, int rec)
-{
-    if (DT == SHM_F32) return reinterpret_cast<const float4*>(table)[rec];
-    const uint2 v = reinterpret_cast<const uint2*>(table)[rec];
-    return DT == SHM_F16 ? h4_to_f4(v) : b4_to_f4(v);
-}
 
 template <int DT>
 __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_t table_bytes)
@@ -66,8 +25,8 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_abort;
     const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem);
-    const unsigned char* table = smem + TABLE_OFFSET;
-    const uint32_t table_s = bar + TABLE_OFFSET;
+    const unsigned char* table = smem + stage::TABLE_OFFSET;
+    const uint32_t table_s = bar + stage::TABLE_OFFSET;
     const int tid = threadIdx.x;
     const int G = a.L.n_glyphs, N = a.L.N_uniform, P = N + 2;
     const float qnan = __int_as_float(0x7fc00000);
@@ -92,8 +51,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
     }
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stage::init(bar);
         s_abort = 0;
     }
     __syncthreads();
@@ -103,31 +61,18 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
         const int64_t s0 = min(max(__ldg(a.seg + g), (int64_t)0), a.Q);
         const int64_t s1 = min(max(__ldg(a.seg + g + 1), s0), a.Q);
         if (s1 <= s0) continue;  // block-uniform
-        if (tid == 0) {
-            // the previous glyph's table was read through the generic proxy: order those reads
-            // before the async-proxy writes of the copy
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(table_bytes)
-                         : "memory");
-            const unsigned char* src = reinterpret_cast<const unsigned char*>(a.L.data) +
-                                       (size_t)g * (size_t)table_bytes;
-            for (uint32_t off = 0; off < table_bytes; off += BULK_PIECE) {
-                const uint32_t n = min(BULK_PIECE, table_bytes - off);
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                    ::"r"(table_s + off), "l"(src + off), "r"(n), "r"(bar)
-                    : "memory");
-            }
-        }
+        if (tid == 0)
+            stage::issue(bar, table_s, reinterpret_cast<const unsigned char*>(a.L.data) + (size_t)g * table_bytes,
+                         table_bytes);
         // first direction of this thread while the copy runs
         int64_t q = s0 + tid;
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
         if (q < s1) { d0 = __ldg(a.dirs + 3 * q); d1 = __ldg(a.dirs + 3 * q + 1); d2 = __ldg(a.dirs + 3 * q + 2); }
-        if (!bar_wait(bar, phase, STAGE_WAIT_NS)) s_abort = 1;
+        if (!stage::bar_wait(bar, phase, stage::WAIT_NS)) s_abort = 1;
         __syncthreads();
         if (s_abort) {
             status |= SHM_DEV_TIMEOUT;
-            if (tid == 0) bar_wait(bar, phase, STAGE_DRAIN_NS);
+            if (tid == 0) stage::bar_wait(bar, phase, stage::DRAIN_NS);
             break;
         }
         phase ^= 1;
@@ -144,12 +89,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
                 float s, t;
                 cell_of(pick3(c.k1, d0, d1, d2), c.m, c.im, N, i, s);
                 cell_of(pick3(c.k2, d0, d1, d2), c.m, c.im, N, j, t);
-                const int rec = (c.f * P + j) * P + i;
-                Corners cr;
-                cr.c00 = smem_rec<DT>(table, rec);
-                cr.c10 = smem_rec<DT>(table, rec + 1);
-                cr.c01 = smem_rec<DT>(table, rec + P);
-                cr.c11 = smem_rec<DT>(table, rec + P + 1);
+                const Corners cr = stage::corners<DT>(table, P, c.f, i, j);
                 const HermOut h = hermite2(cr, s, t);
                 R = r0 + h.r;
                 Ru = (float)N * h.rs;
@@ -175,7 +115,7 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
 template <int DT>
 cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
 {
-    const int smem = TABLE_OFFSET + (int)table_bytes;
+    const int smem = stage::TABLE_OFFSET + (int)table_bytes;
     static int configured = -1;
     if (configured != smem) {
         cudaError_t e = cudaFuncSetAttribute(k_query_staged<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
