@@ -477,6 +477,81 @@ __global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_s
     store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
 }
 
+// Whole-face variant for tables up to N = FACE_N_MAX: one CTA per (glyph, face) evaluates the
+// (N+4)^2 margin samples once into shared memory (no halo re-evaluation: a 16x16 tile needs 18x18
+// samples, up to 3.2x the face's count at N = 16) and then forms the records.  Same arithmetic per
+// sample and per record as k_fd_build.
+constexpr int FACE_N_MAX = 144;  // (N+4)^2 floats <= 87.6 KB
+
+template <class Map>
+__global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
+{
+    extern __shared__ float Sf[];  // [S][S]
+    __shared__ float bump[MAX_BUMPS_SMEM][5];
+    int unused;
+    const int g = map_block(map, unused), f = blockIdx.y;
+    const GlyphRef Gr = glyph_ref(out, g);
+    const int N = Gr.N, P = N + 2, S = N + 4;
+    const int tid = threadIdx.x;
+    const int k = f >> 1;
+    const float sg = (f & 1) ? -1.0f : 1.0f;
+    const Vec3 a = axis_vec(k, sg), bb = axis_vec((k + 1) % 3, 1.0f), cc = axis_vec((k + 2) % 3, 1.0f);
+    auto dir = [&](int ii, int jj) {
+        const float X = (float)(2 * ii - 3 - N) / (float)N;
+        const float Y = (float)(2 * jj - 3 - N) / (float)N;
+        const float ir = rsqrtf(1.0f + X * X + Y * Y);
+        return Vec3{(a.x + X * bb.x + Y * cc.x) * ir, (a.y + X * bb.y + Y * cc.y) * ir,
+                    (a.z + X * bb.z + Y * cc.z) * ir};
+    };
+    for (int e = tid; e < S * S; e += 256) {
+        const int ii = e % S, jj = e / S;
+        float v = 0.0f;
+        if (src.kind == SHM_SRC_SAMPLES)
+            v = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
+        else if (src.kind == SHM_SRC_FBM)
+            v = fbm(dir(ii, jj), src);
+        Sf[e] = v;
+    }
+    float base = 0.0f;
+    if (src.kind == SHM_SRC_BUMPS) {
+        base = 1.0f - Gr.r0;
+        const int64_t b_lo = __ldg(src.bump_offset + g), b_hi = __ldg(src.bump_offset + g + 1);
+        for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
+            const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
+            __syncthreads();
+            for (int e = tid; e < nb; e += 256) {
+                bump[e][0] = __ldg(src.mu + 3 * (bc + e));
+                bump[e][1] = __ldg(src.mu + 3 * (bc + e) + 1);
+                bump[e][2] = __ldg(src.mu + 3 * (bc + e) + 2);
+                bump[e][3] = __ldg(src.amp + bc + e);
+                const float wd = __ldg(src.width + bc + e);
+                bump[e][4] = -0.5f / (wd * wd);
+            }
+            __syncthreads();
+            for (int e = tid; e < S * S; e += 256) {
+                const Vec3 w = dir(e % S, e / S);
+                float sum = Sf[e];
+                for (int q = 0; q < nb; ++q) {
+                    const float dx = w.x - bump[q][0], dy = w.y - bump[q][1], dz = w.z - bump[q][2];
+                    sum = fmaf(bump[q][3], expf((dx * dx + dy * dy + dz * dz) * bump[q][4]), sum);
+                }
+                Sf[e] = sum;
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < P * P; e += 256) {
+        const int i = e % P, j = e / P;
+        const float* c = Sf + (j + 1) * S + (i + 1);  // texel (i, j) is sample (i+1, j+1)
+        float4 v;
+        v.x = c[0] + base;
+        v.y = 0.5f * (c[1] - c[-1]);
+        v.z = 0.5f * (c[S] - c[-S]);
+        v.w = 0.25f * ((c[S + 1] - c[-S + 1]) - (c[S - 1] - c[-S - 1]));
+        store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
+    }
+}
+
 static int64_t fd_tiles(int N)
 {
     const int64_t t = (N + 2 + FT - 1) / FT;
@@ -495,6 +570,23 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
         return for_each_glyph_chunk(sz, value_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
             k_fd_build<std::decay_t<decltype(map)>, true><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
         });
+    if (sz.max_N <= FACE_N_MAX) {
+        const int S = sz.max_N + 4;
+        const int smem = S * S * (int)sizeof(float);
+        static int configured[2] = {0, 0};
+        const int mi = sz.N_uniform > 0 ? 0 : 1;
+        if (configured[mi] < smem) {
+            cudaError_t e = (mi == 0) ? cudaFuncSetAttribute(k_fd_face<UniformMap>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                                      : cudaFuncSetAttribute(k_fd_face<TileMap>,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            configured[mi] = smem;
+        }
+        return for_each_glyph_chunk(sz, [](int) { return (int64_t)1; }, [&](unsigned bx, unsigned bz, const auto& map) {
+            k_fd_face<std::decay_t<decltype(map)>><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, map);
+        });
+    }
     return for_each_glyph_chunk(sz, fd_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
         k_fd_build<std::decay_t<decltype(map)>, false><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
     });
