@@ -20,7 +20,7 @@
 //   warp 0 lane 0: TMA producer        warp 1: TMEM allocation; lane 0 issues the MMAs
 //   warps 4-7: epilogue (TMEM lane quadrant = warp % 4), table writes
 // Epilogue of the float32 texel table: per 32 glyphs the four warps transpose their TMEM rows into
-// a [32 glyphs][128 columns] shared box (double-buffered) and one thread writes it with a TMA
+// a [32 glyphs][128 columns] shared box (four boxes in flight) and one thread writes it with a TMA
 // tensor store (512 B contiguous per glyph row).  Plain per-thread stores, 128 B per warp
 // instruction to 32 different table rows, ran the memory write path at ~9 B/clk/SM and left the
 // tensor pipe idle 70 % of the time.  Other dtypes / layouts keep per-thread stores.
@@ -46,7 +46,8 @@ constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int OG = 32;                                // glyphs per output store box
 constexpr uint32_t OUT_BYTES = OG * TM * 4;           // one [32 glyphs][128 columns] f32 box, 16 KB
 constexpr uint32_t BAR_BYTES = 256;
-constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + 2 * OUT_BYTES + BAR_BYTES + 1024;
+constexpr int NOUT = 4;                               // output boxes in flight per CTA
+constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + NOUT * OUT_BYTES + BAR_BYTES + 1024;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;   // 1 s
 constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;   // 100 ms
@@ -134,7 +135,8 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t sr
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// at most NOUT - 1 stores may still be reading their shared boxes
+__device__ __forceinline__ void bulk_wait_read_free() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(NOUT - 1) : "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -204,8 +206,8 @@ __global__ void __launch_bounds__(256, 1)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* obuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);  // 2 x [OG][TM]
-    uint8_t* bars = smem + NSTAGE * STAGE_BYTES + 2 * OUT_BYTES;
+    float* obuf = reinterpret_cast<float*>(smem + NSTAGE * STAGE_BYTES);  // NOUT x [OG][TM]
+    uint8_t* bars = smem + NSTAGE * STAGE_BYTES + NOUT * OUT_BYTES;
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * NSTAGE, tfull0 = empty0 + 8 * NSTAGE,
                    tempty0 = tfull0 + 16, drain = tempty0 + 16;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 128);
@@ -335,8 +337,8 @@ __global__ void __launch_bounds__(256, 1)
                 const int g0 = nt * TN + n0;
                 if (a.direct) {
                     if (g0 >= a.G) continue;  // block-uniform: whole box beyond the last glyph
-                    float* buf = obuf + (box & 1) * (OG * TM);
-                    if (issuer) bulk_wait_read1();  // the store issued two boxes ago has read `buf`
+                    float* buf = obuf + (box % NOUT) * (OG * TM);
+                    if (issuer) bulk_wait_read_free();  // the store issued NOUT boxes ago has read `buf`
                     epi_bar();
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {

@@ -7,8 +7,10 @@
 //   k_sh_gemm       lut[g][t][ch] = sum_k c[g][k] basis[k][t][ch] - r0[g] (ch 0): the bake of many
 //                   glyphs as one [G x K] x [K x 4T] contraction (SIMT float32 reference engine).
 //   k_sh_gemm_bwd   dc[g][k] = sum_{t,ch} dlut[g][t][ch] basis[k][t][ch].
-//   k_fd_build      central differences on a sample grid with a one-texel bake margin, from
-//                   stored samples, Gaussian bumps or value-noise fBm evaluated in the kernel.
+//   k_fd_face       central differences on a sample grid with a one-texel bake margin, from
+//                   stored samples, Gaussian bumps or value-noise fBm evaluated in the kernel
+//                   (per face or 64 x 64 region, samples in shared memory); k_value_build stores
+//                   the samples themselves for value-only tables.
 //   k_pack          re-encode a table into another dtype / layout.
 //   k_bounds        per-glyph bound of |interpolated r| for ray bracketing (§3.1).
 //   k_sh_eval       direct SH value, S^2 gradient and normal (ground truth, no table).
@@ -380,24 +382,22 @@ __device__ float fbm(const Vec3& w, const shm_source& src)
 }
 
 // ------------------------------------------------------------------------------------------
-// FD bake: 16x16 texel tile per CTA, 18x18 samples (one-texel halo) in shared memory.
-constexpr int FT = 16, FS = FT + 2, MAX_BUMPS_SMEM = 128;
+// Sampled sources: value tables (k_value_build) and finite-difference records (k_fd_face).
+constexpr int FS = 18, MAX_BUMPS_SMEM = 128;
 
-// VALUE: the table is a SHM_LAYOUT_VALUE grid, which is the margin sample grid itself: tiles then
-// cover the (N+4)^2 samples directly and store them (plus the value offset), no differences.
-template <class Map, bool VALUE>
-__global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
+// Value tables (SHM_LAYOUT_VALUE) of sampled sources: the table is the margin sample grid itself,
+// so 18 x 18 tiles of samples are evaluated and stored (plus the value offset), no differences.
+template <class Map>
+__global__ void __launch_bounds__(256) k_value_build(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
 {
-    __shared__ float Sm[FS][FS];
     __shared__ float bump[MAX_BUMPS_SMEM][5];
     int tile;
     const int g = map_block(map, tile), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
-    const int N = Gr.N, P = N + 2, S = N + 4;
-    const int step = VALUE ? FS : FT;
-    const int tiles = ((VALUE ? S : P) + step - 1) / step;
+    const int N = Gr.N, S = N + 4;
+    const int tiles = (S + FS - 1) / FS;
     if (tile >= tiles * tiles) return;
-    const int i0 = (tile % tiles) * step, j0 = (tile / tiles) * step;
+    const int i0 = (tile % tiles) * FS, j0 = (tile / tiles) * FS;
     const int tid = threadIdx.x;
     const int k = f >> 1;
     const float sg = (f & 1) ? -1.0f : 1.0f;
@@ -451,51 +451,43 @@ __global__ void __launch_bounds__(256) k_fd_build(LutView out, void* data, shm_s
             }
         }
     }
-    if constexpr (VALUE) {
-        for (int r = 0; r < 2; ++r) {
-            if (!live[r]) continue;
-            const int e = tid + r * 256;
-            const int ii = i0 + (e % FS), jj = j0 + (e / FS);
-            store_val(data, out.dtype, Gr.base + ((int64_t)f * S + jj) * S + ii, acc[r] + base);
-        }
-        return;
-    }
     for (int r = 0; r < 2; ++r) {
+        if (!live[r]) continue;
         const int e = tid + r * 256;
-        if (e < FS * FS) Sm[e / FS][e % FS] = acc[r];
+        const int ii = i0 + (e % FS), jj = j0 + (e / FS);
+        store_val(data, out.dtype, Gr.base + ((int64_t)f * S + jj) * S + ii, acc[r] + base);
     }
-    __syncthreads();
-    const int ti = tid % FT, tj = tid / FT;
-    const int i = i0 + ti, j = j0 + tj;
-    if (i >= P || j >= P) return;
-    const int si = ti + 1, sj = tj + 1;  // texel (i, j) is sample (i+1, j+1): tile-local (ti+1, tj+1)
-    float4 v;
-    v.x = Sm[sj][si] + base;
-    v.y = 0.5f * (Sm[sj][si + 1] - Sm[sj][si - 1]);
-    v.z = 0.5f * (Sm[sj + 1][si] - Sm[sj - 1][si]);
-    v.w = 0.25f * ((Sm[sj + 1][si + 1] - Sm[sj - 1][si + 1]) - (Sm[sj + 1][si - 1] - Sm[sj - 1][si - 1]));
-    store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
 }
 
-// Whole-face variant for tables up to N = FACE_N_MAX: one CTA per (glyph, face) evaluates the
-// (N+4)^2 margin samples once into shared memory (no halo re-evaluation: a 16x16 tile needs 18x18
-// samples, up to 3.2x the face's count at N = 16) and then forms the records.  Same arithmetic per
-// sample and per record as k_fd_build.
+// Region variant: one CTA per (glyph, face, T x T texel region) evaluates the region's
+// (T+2)^2 margin samples once into shared memory, then forms its records.  For tables up to
+// N = FACE_N_MAX the region is the whole padded face (no sample is evaluated twice; a 16x16 tile
+// needs 18x18 samples, up to 3.2x the face's count at N = 16); larger tables use 64x64 regions
+// (6 % re-evaluation at the region borders).  The sample directions and values are those
+// of the value tables (k_value_build).
 constexpr int FACE_N_MAX = 144;  // (N+4)^2 floats <= 87.6 KB
+constexpr int REGION_T = 64;     // region edge for larger tables: 66^2 floats = 17.4 KB
 
 template <class Map>
-__global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
+__global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_source src, int T,
+                                                 const __grid_constant__ Map map)
 {
-    extern __shared__ float Sf[];  // [S][S]
+    extern __shared__ float Sf[];  // [T+2][T+2]
     __shared__ float bump[MAX_BUMPS_SMEM][5];
-    int unused;
-    const int g = map_block(map, unused), f = blockIdx.y;
+    int region;
+    const int g = map_block(map, region), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
-    const int N = Gr.N, P = N + 2, S = N + 4;
+    const int N = Gr.N, P = N + 2;
+    const int nr = (P + T - 1) / T;
+    if (region >= nr * nr) return;
+    const int i0 = (region % nr) * T, j0 = (region / nr) * T;  // first texel of the region
+    const int ti = min(T, P - i0), tj = min(T, P - j0);      // texels in the region
+    const int Si = ti + 2, Sj = tj + 2;                       // samples: texels i0-1 .. i0+ti
     const int tid = threadIdx.x;
     const int k = f >> 1;
     const float sg = (f & 1) ? -1.0f : 1.0f;
     const Vec3 a = axis_vec(k, sg), bb = axis_vec((k + 1) % 3, 1.0f), cc = axis_vec((k + 2) % 3, 1.0f);
+    // sample-grid index (ii, jj) of the face (texel (ii-1, jj-1)); local sample (li, lj) = (ii-i0, jj-j0)
     auto dir = [&](int ii, int jj) {
         const float X = (float)(2 * ii - 3 - N) / (float)N;
         const float Y = (float)(2 * jj - 3 - N) / (float)N;
@@ -503,8 +495,9 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
         return Vec3{(a.x + X * bb.x + Y * cc.x) * ir, (a.y + X * bb.y + Y * cc.y) * ir,
                     (a.z + X * bb.z + Y * cc.z) * ir};
     };
-    for (int e = tid; e < S * S; e += 256) {
-        const int ii = e % S, jj = e / S;
+    const int S = N + 4;
+    for (int e = tid; e < Si * Sj; e += 256) {
+        const int ii = i0 + e % Si, jj = j0 + e / Si;
         float v = 0.0f;
         if (src.kind == SHM_SRC_SAMPLES)
             v = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
@@ -528,8 +521,8 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                 bump[e][4] = -0.5f / (wd * wd);
             }
             __syncthreads();
-            for (int e = tid; e < S * S; e += 256) {
-                const Vec3 w = dir(e % S, e / S);
+            for (int e = tid; e < Si * Sj; e += 256) {
+                const Vec3 w = dir(i0 + e % Si, j0 + e / Si);
                 float sum = Sf[e];
                 for (int q = 0; q < nb; ++q) {
                     const float dx = w.x - bump[q][0], dy = w.y - bump[q][1], dz = w.z - bump[q][2];
@@ -540,22 +533,16 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
         }
     }
     __syncthreads();
-    for (int e = tid; e < P * P; e += 256) {
-        const int i = e % P, j = e / P;
-        const float* c = Sf + (j + 1) * S + (i + 1);  // texel (i, j) is sample (i+1, j+1)
+    for (int e = tid; e < ti * tj; e += 256) {
+        const int li = e % ti, lj = e / ti;
+        const float* c = Sf + (lj + 1) * Si + (li + 1);  // texel (i0+li, j0+lj) is local sample (li+1, lj+1)
         float4 v;
         v.x = c[0] + base;
         v.y = 0.5f * (c[1] - c[-1]);
-        v.z = 0.5f * (c[S] - c[-S]);
-        v.w = 0.25f * ((c[S + 1] - c[-S + 1]) - (c[S - 1] - c[-S - 1]));
-        store_texel(data, out.dtype, out.layout, Gr, f, j, i, v);
+        v.z = 0.5f * (c[Si] - c[-Si]);
+        v.w = 0.25f * ((c[Si + 1] - c[-Si + 1]) - (c[Si - 1] - c[-Si - 1]));
+        store_texel(data, out.dtype, out.layout, Gr, f, j0 + lj, i0 + li, v);
     }
-}
-
-static int64_t fd_tiles(int N)
-{
-    const int64_t t = (N + 2 + FT - 1) / FT;
-    return t * t;
 }
 
 static int64_t value_tiles(int N)
@@ -568,11 +555,11 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
 {
     if (out.layout == SHM_LAYOUT_VALUE)
         return for_each_glyph_chunk(sz, value_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
-            k_fd_build<std::decay_t<decltype(map)>, true><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
+            k_value_build<std::decay_t<decltype(map)>><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
         });
-    if (sz.max_N <= FACE_N_MAX) {
-        const int S = sz.max_N + 4;
-        const int smem = S * S * (int)sizeof(float);
+    {
+        const int T = (sz.max_N <= FACE_N_MAX) ? sz.max_N + 2 : REGION_T;
+        const int smem = (T + 2) * (T + 2) * (int)sizeof(float);
         static int configured[2] = {0, 0};
         const int mi = sz.N_uniform > 0 ? 0 : 1;
         if (configured[mi] < smem) {
@@ -583,13 +570,14 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
             if (e != cudaSuccess) return e;
             configured[mi] = smem;
         }
-        return for_each_glyph_chunk(sz, [](int) { return (int64_t)1; }, [&](unsigned bx, unsigned bz, const auto& map) {
-            k_fd_face<std::decay_t<decltype(map)>><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, map);
+        auto regions = [T](int N) {
+            const int64_t r = (N + 2 + T - 1) / T;
+            return r * r;
+        };
+        return for_each_glyph_chunk(sz, regions, [&](unsigned bx, unsigned bz, const auto& map) {
+            k_fd_face<std::decay_t<decltype(map)>><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, T, map);
         });
     }
-    return for_each_glyph_chunk(sz, fd_tiles, [&](unsigned bx, unsigned bz, const auto& map) {
-        k_fd_build<std::decay_t<decltype(map)>, false><<<dim3(bx, 6, bz), 256, 0, s>>>(out, data, src, map);
-    });
 }
 
 // ------------------------------------------------------------------------------------------
