@@ -220,6 +220,10 @@ class GlyphField:
                     for k, s in (("R", (self.Q,)), ("grad", (self.Q, 3)), ("normal", (self.Q, 3)))}
         self.src = S.Source(kind=S.SHM_SRC_SH, L=self.L, coeffs=self.coeffs, basis=self.basis)
         self.ws = S.build_workspace(self.lut, self.src) if self.engine == "tcgen05" else None
+        # launch shape of the query picked by the library's tuner on this batch (kept for the run)
+        S.build_lut(self.lut, self.src, ws=self.ws)
+        self.tuned = S.tune_query(self.lut, self.dirs, seg=self.seg, reps=3)
+        self.config["query_launch_shape"] = self.tuned
         # tcgen05 engine: coefficient split + contraction; CUDA-core engine: one contraction kernel
         self.launches_per_step = 3 if self.engine == "tcgen05" else 2
 
@@ -476,6 +480,10 @@ class Planet:
         for s0, d in I.directions_chunked(self.Qr, self.seed + 11):
             self.dr[s0:s0 + len(d)].copy_(torch.from_numpy(d))
         self.dc = torch.from_numpy(I.coherent_sphere_directions(self.Qc, n_frames=128)).to(dev)
+        # launch shape of the per-query kernel picked by the library's tuner (random batch)
+        self.bake()
+        self.tuned = S.tune_query(self.lut, self.dr, reps=2)
+        self.config["query_launch_shape"] = self.tuned
         self.out = {k: torch.empty(s, dtype=torch.float32, device=dev)
                     for k, s in (("R", (self.Qr,)), ("grad", (self.Qr, 3)), ("normal", (self.Qr, 3)))}
         self.launches_per_step = 3 if (self.dtype == 0 and self.layout == 0) else 4

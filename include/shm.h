@@ -9,8 +9,9 @@
  *
  * Conventions (every entry point):
  *   - All array pointers are DEVICE pointers owned by the caller, unless a comment says host.
- *     The library allocates no device memory and keeps no state between calls (the one
- *     exception is the static workspace of shm_raycast_noalloc, described there).
+ *     The library allocates no device memory and keeps no state between calls, except the
+ *     static workspace of shm_raycast_noalloc and the launch-shape table of shm_tune_query
+ *     (both described there).
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  *     The returned status covers host-side argument validation and launch errors only.
  *   - Conditions found on the device never trap: they are OR-ed into *dev_status (device
@@ -111,6 +112,22 @@ shm_status shm_lut_layout(int32_t G, const int32_t* N_host, int32_t dtype, int32
 shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
                      const int64_t* seg, float* R, float* grad, float* normal, float* chart,
                      int32_t* fij, int32_t* dev_status, shm_stream stream);
+
+/* Launch-shape autotuning of shm_query (no counterpart in the paper).  Times every launch shape
+ * of the kernel that shm_query would use for these arguments -- for per-glyph segments on small
+ * uniform tables the shared-memory staged kernel (threads per CTA 512 / 1,024 / 256), otherwise
+ * the per-query kernel ((threads per CTA, rounds per CTA chunk) = (512, 8), (256, 16), (1024, 4),
+ * (256, 8)) -- `reps` times each on `stream` (writing the outputs), and records the fastest for
+ * the current device, that path, dtype and layout; later shm_query calls use it.  Results do not
+ * depend on the shape (same arithmetic per query).  Synchronises `stream`; not for use while a
+ * CUDA graph is being captured.  *chosen (host, may be NULL) receives the shape index,
+ * times_ms (host [SHM_TUNE_MAX_SHAPES], may be NULL) the mean time per shape (-1 = not tried).
+ * The table is process-wide; shm_tune_reset() restores the defaults (shape 0). */
+#define SHM_TUNE_MAX_SHAPES 4
+shm_status shm_tune_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
+                          const int64_t* seg, float* R, float* grad, float* normal, int32_t reps,
+                          int32_t* chosen, float* times_ms, shm_stream stream);
+shm_status shm_tune_reset(void);
 
 /* Value-only reconstruction baselines (§4.2 Table psnr_value, §4.5 Table cost_extended) on a
  * SHM_LAYOUT_VALUE table, with the chart, glyph selection, outputs and status rules of shm_query.

@@ -69,6 +69,8 @@ _SIGS = {
     "shm_lut_layout": (C.c_int, [_I32, _VP, _I32, _I32, _VP, _VP]),
     "shm_query": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_query_recon": (C.c_int, [_VP, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_tune_query": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
+    "shm_tune_reset": (C.c_int, []),
     "shm_sh_basis_bytes": (C.c_int64, [_I32, _I32]),
     "shm_sh_basis": (C.c_int, [_I32, _I32, _VP, _VP]),
     "shm_build_lut": (C.c_int, [_VP, _VP, _VP, _SZ, _VP]),
@@ -252,6 +254,28 @@ def query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.T
 
 
 # ------------------------------------------------------------------------------------------- bake
+def tune_query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.Tensor = None, reps: int = 3,
+               stream=None) -> dict:
+    """shm_tune_query: time the launch shapes of shm_query on this batch and keep the fastest for
+    later calls.  Returns {"chosen": index, "times_ms": [per shape, -1 = not tried]}."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    _need(glyph, torch.int32, (Q,), "glyph")
+    _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
+    out = {k: torch.empty(s, dtype=torch.float32, device=dirs.device)
+           for k, s in (("R", (Q,)), ("grad", (Q, 3)), ("normal", (Q, 3)))}
+    chosen = C.c_int32(-1)
+    times = (C.c_float * 4)()
+    _check(lib().shm_tune_query(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(out["R"]),
+                                _ptr(out["grad"]), _ptr(out["normal"]), int(reps), C.byref(chosen), times,
+                                _stream(stream)), "shm_tune_query")
+    return {"chosen": chosen.value, "times_ms": [round(float(t), 5) for t in times]}
+
+
+def tune_reset():
+    _check(lib().shm_tune_reset(), "shm_tune_reset")
+
+
 def query_recon(lut: Lut, method: int, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.Tensor = None,
                 want=("R", "grad", "normal"), out: dict = None, dev_status: torch.Tensor = None, stream=None) -> dict:
     """shm_query_recon: value-only reconstruction baseline `method` on a SHM_LAYOUT_VALUE table."""

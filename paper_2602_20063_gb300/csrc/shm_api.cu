@@ -135,6 +135,62 @@ shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int
     return map_cuda(launch_query_fwd(a, (cudaStream_t)stream));
 }
 
+shm_status shm_tune_query(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph, const int64_t* seg,
+                          float* R, float* grad, float* normal, int32_t reps, int32_t* chosen, float* times_ms,
+                          shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
+    if (Q <= 0 || !dirs || reps < 1 || reps > 1000) return SHM_ERR_INVALID_ARG;
+    QueryArgs a;
+    a.L = view(lut);
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = glyph;
+    a.seg = glyph ? nullptr : seg;
+    a.R = R;
+    a.grad = grad;
+    a.normal = normal;
+    a.chart = nullptr;
+    a.fij = nullptr;
+    a.dev_status = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = query_shapes(a);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SHM_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SHM_ERR_CUDA; }
+    int best = 0;
+    float best_ms = 0.0f;
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < SHM_TUNE_MAX_SHAPES && times_ms; ++k) times_ms[k] = -1.0f;
+    for (int k = 0; k < n && err == cudaSuccess; ++k) {
+        err = launch_query_shape(a, k, s);  // warm-up (first-use attributes, caches)
+        if (err == cudaSuccess) err = cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_query_shape(a, k, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) break;
+        ms /= (float)reps;
+        if (times_ms && k < SHM_TUNE_MAX_SHAPES) times_ms[k] = ms;
+        if (k == 0 || ms < best_ms) { best = k; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return SHM_ERR_CUDA;
+    set_tuned_query_shape(a, best);
+    if (chosen) *chosen = best;
+    return SHM_OK;
+}
+
+shm_status shm_tune_reset(void)
+{
+    reset_tuned_shapes();
+    return SHM_OK;
+}
+
 shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const float* dirs, const int32_t* glyph,
                            const int64_t* seg, float* R, float* grad, float* normal, float* chart, int32_t* fij,
                            int32_t* dev_status, shm_stream stream)

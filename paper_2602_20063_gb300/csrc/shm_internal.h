@@ -130,7 +130,15 @@ cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s);
 // Glyph tables up to this size are staged whole in shared memory by the segment query (two CTAs
 // of 512 threads per SM: (232,448 - 2 x 1 KB reserved) / 2 minus the barrier block).
 constexpr int64_t STAGED_TABLE_MAX_BYTES = 114688;
-cudaError_t launch_query_staged(const QueryArgs& a, cudaStream_t s);
+cudaError_t launch_query_staged(const QueryArgs& a, int shape, cudaStream_t s);
+int staged_shapes();
+// Launch shapes and the per-device tuning table (shm_query.cu).
+bool query_is_staged(const QueryArgs& a);
+int query_shapes(const QueryArgs& a);
+cudaError_t launch_query_shape(const QueryArgs& a, int shape, cudaStream_t s);
+int tuned_query_shape(const QueryArgs& a);
+void set_tuned_query_shape(const QueryArgs& a, int shape);
+void reset_tuned_shapes();
 cudaError_t launch_gather_probe(const void* table, int64_t table_bytes, int block_bytes, int64_t Q, const float* in,
                                 float* out, cudaStream_t s);
 cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s);

@@ -15,11 +15,16 @@
 
 namespace shm {
 
-constexpr int QBLOCK = 512;      // threads per CTA
-constexpr int QIT = 8;           // iterations per CTA chunk: a CTA takes QBLOCK * QIT = 4,096 consecutive queries
-constexpr int QMINBLOCKS = 2;    // <= 64 registers; 32 resident warps per SM
+// Launch shapes (threads per CTA, rounds per CTA chunk): a CTA takes BLOCK * IT consecutive
+// queries.  Shape 0 is the default; shm_tune_query times the others on a caller's batch and
+// records the fastest per (path, dtype, layout) for later calls.
+struct QShape {
+    int block, it;
+};
+constexpr int N_QSHAPES = 4;
+constexpr QShape QSHAPES[N_QSHAPES] = {{512, 8}, {256, 16}, {1024, 4}, {256, 8}};
 
-// Work is handed out per CTA in contiguous chunks of 4,096 queries, so that for per-glyph query
+// Work is handed out per CTA in contiguous chunks (4,096 queries by default), so that for per-glyph query
 // segments a CTA serves whole glyphs and the glyph's table stays in that SM's L1 (two CTAs per SM
 // keep two tables of up to ~110 KB resident) instead of being pulled into several SMs.
 //
@@ -28,14 +33,15 @@ constexpr int QMINBLOCKS = 2;    // <= 64 registers; 32 resident warps per SM
 // written with 24 128-bit stores, re-distributed through a 384-byte per-warp shared buffer, so a
 // warp issues 1 + 4 + 3 global memory instructions per round instead of 3 + 4 + 7 (the load/store
 // queue, not DRAM, limited the random-access case).  Partial rounds use scalar accesses.
-// The 16-tap baselines need more than 64 registers: one resident CTA per SM for them.
-template <int RECON>
+// The Hermite query keeps <= 64 registers (1,024 resident threads per SM); the 16-tap baselines
+// need more than 64 registers: one resident CTA of 512 per SM for them.
+template <int RECON, int QBLOCK>
 struct QueryOccupancy {
-    static constexpr int min_blocks = (RECON >= SHM_RECON_BICUBIC) ? 1 : QMINBLOCKS;
+    static constexpr int min_blocks = (RECON >= SHM_RECON_BICUBIC) ? 1 : (QBLOCK >= 1024 ? 1 : 1024 / QBLOCK);
 };
 
-template <int DT, int LAYOUT, bool VEC, int RECON>
-__global__ void __launch_bounds__(QBLOCK, QueryOccupancy<RECON>::min_blocks) k_query_fwd(QueryArgs a)
+template <int DT, int LAYOUT, bool VEC, int RECON, int QBLOCK = 512, int QIT = 8>
+__global__ void __launch_bounds__(QBLOCK, (QueryOccupancy<RECON, QBLOCK>::min_blocks)) k_query_fwd(QueryArgs a)
 {
     __shared__ __align__(16) float sbuf[QBLOCK / 32][96];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -165,35 +171,37 @@ __global__ void __launch_bounds__(QBLOCK, QueryOccupancy<RECON>::min_blocks) k_q
     report_status(a.dev_status, status);
 }
 
-template <int DT, int LAYOUT, bool VEC, int RECON>
+template <int DT, int LAYOUT, bool VEC, int RECON, int QBLOCK, int QIT>
 cudaError_t launch_fwd_v(const QueryArgs& a, cudaStream_t s)
 {
     // one persistent wave: SMs x resident blocks per SM
     static int resident = 0;
     if (resident == 0) {
         int r = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_query_fwd<DT, LAYOUT, VEC, RECON>, QBLOCK, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_query_fwd<DT, LAYOUT, VEC, RECON, QBLOCK, QIT>, QBLOCK,
+                                                          0) != cudaSuccess ||
             r < 1)
-            r = QueryOccupancy<RECON>::min_blocks;
+            r = QueryOccupancy<RECON, QBLOCK>::min_blocks;
         resident = r;
     }
     int64_t blocks = (a.Q + (int64_t)QBLOCK * QIT - 1) / ((int64_t)QBLOCK * QIT);
     const int64_t cap = (int64_t)sm_count() * resident;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_query_fwd<DT, LAYOUT, VEC, RECON><<<(unsigned)blocks, QBLOCK, 0, s>>>(a);
+    k_query_fwd<DT, LAYOUT, VEC, RECON, QBLOCK, QIT><<<(unsigned)blocks, QBLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 // The vector I/O path measured 4 % faster on uniform random queries of one large table and 7 %
 // slower on per-glyph CSR segments (GB300, 2^28 planet queries / 2^26 glyph-field queries), so it
 // is used when there are no segments and the buffers are 16-byte aligned.
-template <int DT, int LAYOUT, int RECON>
+template <int DT, int LAYOUT, int RECON, int QBLOCK = 512, int QIT = 8>
 cudaError_t launch_fwd_t(const QueryArgs& a, cudaStream_t s)
 {
     const auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-    if (!a.seg && al16(a.dirs) && al16(a.grad) && al16(a.normal)) return launch_fwd_v<DT, LAYOUT, true, RECON>(a, s);
-    return launch_fwd_v<DT, LAYOUT, false, RECON>(a, s);
+    if (!a.seg && al16(a.dirs) && al16(a.grad) && al16(a.normal))
+        return launch_fwd_v<DT, LAYOUT, true, RECON, QBLOCK, QIT>(a, s);
+    return launch_fwd_v<DT, LAYOUT, false, RECON, QBLOCK, QIT>(a, s);
 }
 
 }  // namespace shm

@@ -17,10 +17,14 @@ namespace shm {
 
 namespace {
 
-constexpr int SBLOCK = 512;
+// Launch shapes of the staged kernel: threads per CTA (shape 0 = 512, the default; 1 = 1,024;
+// 2 = 256), with <= 64 registers so that 1,024 threads per SM fit; how many CTAs actually share
+// an SM is set by the table's shared-memory footprint.
+constexpr int N_SSHAPES = 3;
+constexpr int SSHAPES[N_SSHAPES] = {512, 1024, 256};
 
-template <int DT>
-__global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_t table_bytes)
+template <int DT, int SBLOCK>
+__global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArgs a, uint32_t table_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_abort;
@@ -112,37 +116,49 @@ __global__ void __launch_bounds__(SBLOCK, 2) k_query_staged(QueryArgs a, uint32_
     report_status(a.dev_status, status);
 }
 
-template <int DT>
+template <int DT, int SBLOCK>
 cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
 {
     const int smem = stage::TABLE_OFFSET + (int)table_bytes;
     static int configured = -1;
     if (configured != smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_query_staged<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_query_staged<DT, SBLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
     int resident = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT>, SBLOCK, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT, SBLOCK>, SBLOCK, smem) != cudaSuccess ||
         resident < 1)
         resident = 1;
     int64_t blocks = (int64_t)sm_count() * resident;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     if (blocks < 1) blocks = 1;
-    k_query_staged<DT><<<(unsigned)blocks, SBLOCK, smem, s>>>(a, table_bytes);
+    k_query_staged<DT, SBLOCK><<<(unsigned)blocks, SBLOCK, smem, s>>>(a, table_bytes);
     return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_staged_shape(const QueryArgs& a, uint32_t table_bytes, int shape, cudaStream_t s)
+{
+    switch (shape) {
+    case 1: return launch_staged_t<DT, 1024>(a, table_bytes, s);
+    case 2: return launch_staged_t<DT, 256>(a, table_bytes, s);
+    default: return launch_staged_t<DT, 512>(a, table_bytes, s);
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_query_staged(const QueryArgs& a, cudaStream_t s)
+int staged_shapes() { return N_SSHAPES; }
+
+cudaError_t launch_query_staged(const QueryArgs& a, int shape, cudaStream_t s)
 {
     const int64_t P = (int64_t)a.L.N_uniform + 2;
     const int64_t rb = (a.L.dtype == SHM_F32) ? 16 : 8;
     const uint32_t table_bytes = (uint32_t)(6 * P * P * rb);
-    if (a.L.dtype == SHM_F32) return launch_staged_t<SHM_F32>(a, table_bytes, s);
-    if (a.L.dtype == SHM_F16) return launch_staged_t<SHM_F16>(a, table_bytes, s);
-    return launch_staged_t<SHM_BF16>(a, table_bytes, s);
+    if (a.L.dtype == SHM_F32) return launch_staged_shape<SHM_F32>(a, table_bytes, shape, s);
+    if (a.L.dtype == SHM_F16) return launch_staged_shape<SHM_F16>(a, table_bytes, shape, s);
+    return launch_staged_shape<SHM_BF16>(a, table_bytes, shape, s);
 }
 
 }  // namespace shm
