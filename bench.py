@@ -193,6 +193,7 @@ class GlyphField:
         self.Q = self.G * self.per
         self.dtype, self.layout = args.dtype_id, args.layout_id
         self.engine = args.engine
+        self.e2e_chunks_n, self.e2e_streams_n = args.e2e_chunks, args.e2e_streams
         self.seed = 20063 + 1 + 1000 * rank
         import shm_inputs as I
         self.c_host = I.sh_coeffs(self.G, self.L, self.seed).astype(np.float32)
@@ -246,12 +247,12 @@ class GlyphField:
         for st in self.e2e_streams:
             st.wait_stream(main)
         for c, (lut_c, src_c, seg_c, g0, g1) in enumerate(self.e2e_chunks):
-            st = self.e2e_streams[c % 2]
+            st = self.e2e_streams[c % len(self.e2e_streams)]
             q0, q1 = g0 * self.per, g1 * self.per
             with torch.cuda.stream(st):
                 self.dirs[q0:q1].copy_(self.dirs_host[q0:q1], non_blocking=True)
                 self.coeffs[g0:g1].copy_(self.c_pinned[g0:g1], non_blocking=True)
-                S.build_lut(lut_c, src_c, ws=self.e2e_ws[c % 2], stream=st)
+                S.build_lut(lut_c, src_c, ws=self.e2e_ws[c % len(self.e2e_streams)], stream=st)
                 out_c = {k: v[q0:q1] for k, v in self.out.items()}
                 S.query(lut_c, self.dirs[q0:q1], seg=seg_c, out=out_c, stream=st)
                 for k in ("R", "grad", "normal"):
@@ -259,13 +260,14 @@ class GlyphField:
         for st in self.e2e_streams:
             main.wait_stream(st)
 
-    def e2e_setup(self, chunks=8):
+    def e2e_setup(self):
+        chunks, streams = self.e2e_chunks_n, self.e2e_streams_n
         torch, S = self.torch, self.S
         self.c_pinned = torch.from_numpy(self.c_host).pin_memory()
         host_out = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in self.out.items()}
         h2d = self.dirs.numel() * 4 + self.coeffs.numel() * 4
         d2h = sum(v.numel() * 4 for v in self.out.values())
-        self.e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        self.e2e_streams = [torch.cuda.Stream() for _ in range(streams)]
         per_glyph = S.records_per_glyph(self.N, self.layout) * S.record_bytes(self.dtype, self.layout)
         elem = self.lut.data.element_size()
         self.e2e_chunks = []
@@ -278,8 +280,8 @@ class GlyphField:
             seg_c = (self.seg[g0:g1 + 1] - self.seg[g0]).contiguous()
             self.e2e_chunks.append((lut_c, src_c, seg_c, g0, g1))
         ws_c = self.e2e_chunks[0][1]
-        self.e2e_ws = ([S.build_workspace(self.e2e_chunks[0][0], ws_c) for _ in range(2)]
-                       if self.engine == "tcgen05" else [None, None])
+        self.e2e_ws = ([S.build_workspace(self.e2e_chunks[0][0], ws_c) for _ in range(streams)]
+                       if self.engine == "tcgen05" else [None] * streams)
         return host_out, h2d, d2h
 
     def roofline_terms(self, peaks, kernel_ms, sms):
@@ -1105,6 +1107,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=16,
+                    help="glyph field end to end: glyph chunks per step (copies and kernels of neighbouring chunks overlap)")
+    ap.add_argument("--e2e-streams", type=int, default=3, help="glyph field end to end: streams the chunks rotate over")
     args = ap.parse_args()
     args.dtype_id = {"f32": 0, "f16": 1, "bf16": 2}[args.dtype]
     args.layout_id = {"texel": 0, "cell": 1}[args.layout]
