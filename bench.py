@@ -352,9 +352,25 @@ class GlyphField:
                         "note": "value offset r0 = 0.7 per glyph; error vs the same queries on f32 storage"}
             del L16, o16
         del dl
+        ex["write_ceiling"] = self.write_ceiling(torch, timeit, n)
         ex["recon"] = self.recon_extras(S, torch, timeit, n, fwd)
         ex["cuda_graph"] = self.graph_extras(S, torch, timeit, n)
         return ex
+
+    def write_ceiling(self, torch, timeit, n):
+        """Write-only ceiling for the bake, which reads almost nothing and writes the table: a
+        plain device fill (torch's own kernel) of a buffer of the table's size, and the bake's
+        time against it."""
+        nbytes = self.lut.data.numel() * self.lut.data.element_size()
+        buf = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+        ms = timeit(lambda: buf.fill_(1.0), n)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        bake = timeit(lambda: self.S.build_lut(self.lut, self.src, ws=self.ws), n)
+        del buf
+        return {"fill_ms": round(ms, 4), "fill_GBps": round(gbs, 1),
+                "fill_frac_of_measured_copy": round(gbs / load_peaks()["hbm_gbs"], 3),
+                "bake_ms": round(bake, 4), "bake_over_fill_time": round(bake / ms, 3),
+                "note": f"torch fill_ of {nbytes / 1e9:.2f} GB (the glyph table's size), write-only traffic"}
 
     def graph_extras(self, S, torch, timeit, n):
         """The step (bake + query) captured once in a CUDA graph and replayed, against eager launches."""
@@ -460,6 +476,7 @@ class Planet:
         self.Qr = args.planet_queries
         self.Qc = args.planet_queries
         self.dtype, self.layout = args.dtype_id, args.layout_id
+        self.l2g_choice = args.l2_fetch_granularity
         self.seed = 20063 + 3 + 1000 * rank
         import shm_inputs as I
         self.keys = I.fbm_keys(self.seed)
@@ -488,7 +505,34 @@ class Planet:
         self.config["query_launch_shape"] = self.tuned
         self.out = {k: torch.empty(s, dtype=torch.float32, device=dev)
                     for k, s in (("R", (self.Qr,)), ("grad", (self.Qr, 3)), ("normal", (self.Qr, 3)))}
+        self.config["l2_fetch_granularity"] = self.pick_l2_granularity(self.l2g_choice)
         self.launches_per_step = 3 if (self.dtype == 0 and self.layout == 0) else 4
+
+    def pick_l2_granularity(self, choice):
+        """The context's L2 fetch granularity for this process (shm_l2_fetch_granularity): "auto"
+        times one step at 128 B (the behaviour of a fresh context) and at 64 B and keeps the faster.
+        The random query repeated back to back runs 13 % faster at 64 B (more distinct table pieces
+        stay in L2 between repetitions); inside the step, after the bake and the coherent queries,
+        64 B measured 1-2 % slower."""
+        S, torch = self.S, self.torch
+        if choice != "auto":
+            S.l2_fetch_granularity(int(choice))
+            return {"bytes": int(choice), "how": "fixed by --l2-fetch-granularity"}
+        st = torch.cuda.current_stream()
+        times = {}
+        for g in (128, 64):
+            S.l2_fetch_granularity(g)
+            self.step(_NoTimer())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(2):
+                self.step(_NoTimer())
+            e1.record(st)
+            torch.cuda.synchronize()
+            times[g] = e0.elapsed_time(e1) / 2
+        best = min(times, key=times.get)
+        S.l2_fetch_granularity(best)
+        return {"bytes": best, "how": "auto: one step timed at each", "step_ms": {str(k): round(v, 3) for k, v in times.items()}}
 
     def bake(self):
         if self.dtype == 0 and self.layout == 0:
@@ -577,22 +621,29 @@ class Planet:
                         "max_err_grad_rel_vs_f32": float((o["grad"] - ref["grad"]).abs().max()
                                                          / ref["grad"].norm(dim=1).max())}
             del L2, o
-        # random-gather ceiling: the same traffic pattern (12 B in, one aligned block gathered from a
-        # table of the planet's size, 28 B out) without the arithmetic
+        # random-gather ceiling: the same traffic pattern (12 B in, one aligned block of the
+        # footprint's size gathered from a table of the same size as the query's, 28 B out)
+        # without the arithmetic
         probe_out = torch.empty((self.Qr, 7), dtype=torch.float32, device="cuda")
         ceiling = {}
-        for blk, tab_name in ((64, "f32_cell"), (32, "f16_cell")):
-            Lc = S.like_lut(base, dtype=0 if blk == 64 else 1, layout=1)
+        ex["f32_texel"] = {"query_random_ms": round(t_ref, 4)}
+        for blk, dt, ly, tab_name in ((64, 0, 0, "f32_texel"), (64, 0, 1, "f32_cell"), (32, 1, 0, "f16_texel"),
+                                      (32, 1, 1, "f16_cell")):
+            Lc = base if (dt, ly) == (0, 0) else S.like_lut(base, dtype=dt, layout=ly)
+            nb = Lc.data.numel() * Lc.data.element_size()
             ms = timeit(lambda: S.gather_probe(Lc.data, blk, self.dr, out=probe_out))
             q_ms = ex[tab_name]["query_random_ms"]
-            ceiling[f"{blk}B"] = {"probe_ms": round(ms, 4), "items_per_s": self.Qr / (ms * 1e-3),
-                                  "GBps_at_block_plus_40B": (blk + 40) * self.Qr / (ms * 1e-3) / 1e9,
-                                  "frac_of_measured_hbm": round((blk + 40) * self.Qr / (ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"], 3),
-                                  f"query_{tab_name}_over_probe_time": round(q_ms / ms, 3)}
+            ceiling[f"{blk}B_from_{tab_name}_table"] = {
+                "table_MB": round(nb / 1e6, 1), "probe_ms": round(ms, 4), "items_per_s": self.Qr / (ms * 1e-3),
+                "GBps_at_block_plus_40B": (blk + 40) * self.Qr / (ms * 1e-3) / 1e9,
+                "frac_of_measured_hbm": round((blk + 40) * self.Qr / (ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"], 3),
+                f"query_{tab_name}_over_probe_time": round(q_ms / ms, 3)}
             del Lc
-        ceiling["note"] = ("uncorrelated 64 B / 32 B gathers from the matching cell-layout table (1.61 GB f32 / "
-                           "0.81 GB f16: 4 corner records per cell), per item 12 B read + 28 B written; the query on "
-                           "that layout does the same traffic plus the chart, Hermite and S^2 arithmetic")
+        ceiling["note"] = ("uncorrelated aligned gathers of the footprint's bytes (64 B f32, 32 B 16-bit) from a table "
+                           "of the query's table size, per item 12 B read + 28 B written; the query does the same "
+                           "traffic (texel layouts: two row pieces instead of one block) plus the chart, Hermite and "
+                           "S^2 arithmetic.  Items/s fall with table size (100 MB: 41 G/s, 403 MB: 27 G/s, 1.6 GB: "
+                           "20 G/s for 64 B): random 32 B sectors, not streaming bandwidth, set this ceiling")
         ex["random_gather_ceiling"] = ceiling
         del probe_out
         # derivative-consistent mip chain (§4.7) of the f32 texel table: 2048 -> 1024 -> ... -> 16
@@ -1091,7 +1142,7 @@ def run_gpu(args):
     return 0
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -1104,15 +1155,22 @@ def main():
     ap.add_argument("--glyphs", type=int, default=16384)
     ap.add_argument("--per-glyph", type=int, default=4096)
     ap.add_argument("--planet-queries", type=int, default=1 << 28)
+    ap.add_argument("--l2-fetch-granularity", default="auto",
+                    help="planet: L2 fetch granularity in bytes for the process's context, or auto")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=16,
                     help="glyph field end to end: glyph chunks per step (copies and kernels of neighbouring chunks overlap)")
     ap.add_argument("--e2e-streams", type=int, default=3, help="glyph field end to end: streams the chunks rotate over")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     args.dtype_id = {"f32": 0, "f16": 1, "bf16": 2}[args.dtype]
     args.layout_id = {"texel": 0, "cell": 1}[args.layout]
+    return args
+
+
+def main():
+    args = parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -362,6 +362,15 @@ shm_status shm_raycast_noalloc(const shm_lut* lut, const shm_object* objs, int32
 shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t block_bytes, int64_t Q,
                             const float* in, float* out, shm_stream stream);
 
+/* L2 fetch granularity of the calling thread's current device context (a CUDA context limit,
+ * released with the context; no device setting outlives the process): the largest block the L2
+ * fetches from HBM for a miss.  Uncorrelated footprint reads (random directions into an out-of-L2
+ * table) use 16-32 B of each fetch; smaller fetches keep more distinct table pieces in L2.  The
+ * limit is a hint that applies to every kernel launched afterwards in the context, including other
+ * libraries'.  bytes = -1 only reads the current value; 0..128 sets it.  *previous (host, may be
+ * NULL) receives the value before the call.  SHM_ERR_UNSUPPORTED if the device rejects the limit. */
+shm_status shm_l2_fetch_granularity(int32_t bytes, int32_t* previous);
+
 /* ---------------------------------------------------------------- misc */
 
 const char* shm_status_string(shm_status s);

@@ -12,6 +12,6 @@ from .binding import (  # noqa: F401
     Lut, Source, ShmError, alloc_lut, like_lut, lib, lib_path,
     query, query_recon, tune_query, tune_reset, sh_basis, build_lut, build_workspace, build_workspace_bytes, pack_lut, lut_bounds, build_mip, mip_like, mip_chain, query_backward, build_lut_backward, sh_eval, fit_backward, adam_step,
     make_camera, make_raycast_params, objects_tensor, raycast, raycast_noalloc, raycast_workspace_bytes, raycast_query_count,
-    records_per_glyph, record_bytes, gather_probe,
+    records_per_glyph, record_bytes, gather_probe, l2_fetch_granularity,
 )
 from .autograd import query_fn, sh_bake_fn  # noqa: F401

@@ -87,6 +87,7 @@ _SIGS = {
     "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "shm_raycast_noalloc": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_gather_probe": (C.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP]),
+    "shm_l2_fetch_granularity": (C.c_int, [_I32, C.POINTER(C.c_int32)]),
     "shm_status_string": (C.c_char_p, [C.c_int]),
     "shm_version": (C.c_int32, []),
 }
@@ -535,6 +536,14 @@ def raycast_query_count(ws: torch.Tensor) -> int:
 
 
 # ------------------------------------------------------------------------------------------- measurement aid
+def l2_fetch_granularity(nbytes: int = -1) -> int:
+    """shm_l2_fetch_granularity: set the context's L2 fetch granularity hint (0..128 B; -1 only
+    reads it).  Returns the value before the call."""
+    prev = C.c_int32(-1)
+    _check(lib().shm_l2_fetch_granularity(int(nbytes), C.byref(prev)), "shm_l2_fetch_granularity")
+    return prev.value
+
+
 def gather_probe(table: torch.Tensor, block_bytes: int, inp: torch.Tensor, out: torch.Tensor = None, stream=None):
     """shm_gather_probe: the random-gather traffic of a query batch (12 B in, one block gathered,
     28 B out per item) without the arithmetic."""

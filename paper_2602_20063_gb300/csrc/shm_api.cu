@@ -225,6 +225,20 @@ shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t bloc
     return map_cuda(launch_gather_probe(table, table_bytes, block_bytes, Q, in, out, (cudaStream_t)stream));
 }
 
+shm_status shm_l2_fetch_granularity(int32_t bytes, int32_t* previous)
+{
+    if (bytes < -1 || bytes > 128) return SHM_ERR_INVALID_ARG;
+    size_t cur = 0;
+    cudaError_t e = cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity);
+    if (e == cudaErrorUnsupportedLimit) return SHM_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return SHM_ERR_CUDA;
+    if (previous) *previous = (int32_t)cur;
+    if (bytes < 0) return SHM_OK;
+    e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+    if (e == cudaErrorUnsupportedLimit) return SHM_ERR_UNSUPPORTED;
+    return e == cudaSuccess ? SHM_OK : SHM_ERR_CUDA;
+}
+
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
 {
     if (N < 1 || L < 0 || L > 20) return -1;

@@ -170,12 +170,10 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
         dA += (gwa - wk * wdg) * il;
         dB += (gwb - w1 * wdg) * il;
         dC += (gwc - w2 * wdg) * il;
-        // back to Cartesian (a = sigma e_k)
-        float o[3];
-        o[c.k] = dA * c.sigma;
-        o[c.k1] = dB;
-        o[c.k2] = dC;
-        dd = make_float3(o[0], o[1], o[2]);
+        // back to Cartesian (a = sigma e_k): component c.k gets dA sigma, c.k1 dB, c.k2 dC
+        const float sA = dA * c.sigma;
+        dd = make_float3(c.k == 0 ? sA : (c.k1 == 0 ? dB : dC), c.k == 1 ? sA : (c.k1 == 1 ? dB : dC),
+                         c.k == 2 ? sA : (c.k1 == 2 ? dB : dC));
     }
 }
 

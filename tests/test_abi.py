@@ -82,6 +82,9 @@ def test_validation_rejects_bad_arguments_without_a_device(lib):
     L.N = L.offset = 16
     assert lib.shm_build_lut(C.byref(L), C.byref(src), None, 0, None) == 2
     assert lib.shm_sh_basis(0, 4, C.c_void_p(16), None) == 1
+    # L2 fetch granularity outside -1..128 bytes
+    assert lib.shm_l2_fetch_granularity(129, None) == 1
+    assert lib.shm_l2_fetch_granularity(-2, None) == 1
 
 
 def _imports(path):

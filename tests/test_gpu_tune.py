@@ -48,3 +48,21 @@ def test_tune_rejects_bad_arguments(S):
         S.tune_query(L, d, reps=0)
     with pytest.raises(S.ShmError):
         S.tune_query(L, d[:0], reps=1)
+
+
+def test_l2_fetch_granularity_round_trip(S):
+    """shm_l2_fetch_granularity sets the context limit, reports the previous value and leaves query
+    results unchanged (it is a fetch-size hint only)."""
+    N, per = 32, 5000
+    L, _ = upload_pool(S, [O.bake_sh(N, 6, I.sh_coeffs(1, 6, 702)[0])])
+    d = torch.from_numpy(I.directions(per, 703)).cuda()
+    before = S.query(L, d)
+    prev = S.l2_fetch_granularity(-1)
+    assert 0 <= prev <= 128
+    try:
+        assert S.l2_fetch_granularity(32) == prev
+        assert S.l2_fetch_granularity(-1) == 32
+        assert _same(before, S.query(L, d))
+    finally:
+        S.l2_fetch_granularity(prev)
+    assert S.l2_fetch_granularity(-1) == prev

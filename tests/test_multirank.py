@@ -27,8 +27,7 @@ def _worker(rank, world, port, times, out):
     ms = bench.reduce_over_ranks(times[rank], dist, "cpu")
     rate = bench.whole_job_rate(1000.0, world, ms)
     # per-rank replicas draw different inputs (weak scaling)
-    from types import SimpleNamespace
-    args = SimpleNamespace(glyphs=4, per_glyph=8, dtype_id=0, layout_id=0, engine="simt")
+    args = bench.parse_args(["--glyphs", "4", "--per-glyph", "8", "--engine", "simt"])
     w = bench.GlyphField(args, rank)
     out[rank] = (ms, rate, float(w.c_host[0, 1]))
     dist.destroy_process_group()
