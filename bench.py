@@ -645,6 +645,41 @@ class Planet:
                            "S^2 arithmetic.  Items/s fall with table size (100 MB: 41 G/s, 403 MB: 27 G/s, 1.6 GB: "
                            "20 G/s for 64 B): random 32 B sectors, not streaming bandwidth, set this ceiling")
         ex["random_gather_ceiling"] = ceiling
+        # the same probe over table sizes and block sizes (a zero buffer; L2 flushed between runs)
+        big = torch.zeros(3 << 30, dtype=torch.uint8, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+        def timeit_flushed(fn, n=5):
+            fn()
+            ts = []
+            for _ in range(n):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+        sweep = {}
+        for mb in (100, 201, 403, 806, 1612, 3221):
+            tab = big[: mb * 1000 * 1000 // 64 * 64]
+            sweep[f"{mb}MB"] = {f"{blk}B": round(self.Qr / (timeit_flushed(
+                lambda: S.gather_probe(tab, blk, self.dr, out=probe_out)) * 1e-3) / 1e9, 2) for blk in (16, 32, 64)}
+        sweep["unit"] = "G items/s (2^28 uniform random items, 12 B read + one aligned block + 28 B written each)"
+        ex["random_gather_sweep"] = sweep
+        del big, flush
+        # the random query repeated back to back under each context L2 fetch granularity, per launch shape
+        prev = S.l2_fetch_granularity(-1)
+        gran = {}
+        for g in (128, 64, 32):
+            S.l2_fetch_granularity(g)
+            gran[f"{g}B"] = S.tune_query(base, self.dr, reps=3)["times_ms"]
+        S.l2_fetch_granularity(prev)
+        S.tune_query(base, self.dr, reps=2)
+        ex["random_query_back_to_back_by_l2_fetch_granularity"] = {
+            "ms_per_launch_shape": gran, "restored_bytes": prev,
+            "note": "same batch launched repeatedly: table pieces left in L2 by the previous launch are reused"}
         del probe_out
         # derivative-consistent mip chain (§4.7) of the f32 texel table: 2048 -> 1024 -> ... -> 16
         chain = [base]
