@@ -385,12 +385,41 @@ __device__ float fbm(const Vec3& w, const shm_source& src)
 // Sampled sources: value tables (k_value_build) and finite-difference records (k_fd_face).
 constexpr int FS = 18, MAX_BUMPS_SMEM = 128;
 
+// Gaussian bumps of one glyph, staged in shared memory: centre and amplitude as one float4 (a
+// broadcast 16-byte read), and the exponent factor with log2(e) folded in, so that
+//   a exp(-|w - mu|^2 / (2 width^2)) = a exp2(|w - mu|^2 k),  k = -log2(e) / (2 width^2).
+struct BumpSmem {
+    float4 m[MAX_BUMPS_SMEM];
+    float k[MAX_BUMPS_SMEM];
+};
+
+__device__ __forceinline__ void stage_bumps(BumpSmem& B, const shm_source& src, int64_t bc, int nb)
+{
+    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+        B.m[e] = make_float4(__ldg(src.mu + 3 * (bc + e)), __ldg(src.mu + 3 * (bc + e) + 1),
+                             __ldg(src.mu + 3 * (bc + e) + 2), __ldg(src.amp + bc + e));
+        const float wd = __ldg(src.width + bc + e);
+        B.k[e] = -0.72134752044448170f / (wd * wd);  // 0.5 log2(e)
+    }
+}
+
+__device__ __forceinline__ float bump_sum(const BumpSmem& B, int nb, const Vec3& w, float sum)
+{
+#pragma unroll 4
+    for (int q = 0; q < nb; ++q) {
+        const float4 m = B.m[q];
+        const float dx = w.x - m.x, dy = w.y - m.y, dz = w.z - m.z;
+        sum = fmaf(m.w, exp2f((dx * dx + dy * dy + dz * dz) * B.k[q]), sum);
+    }
+    return sum;
+}
+
 // Value tables (SHM_LAYOUT_VALUE) of sampled sources: the table is the margin sample grid itself,
 // so 18 x 18 tiles of samples are evaluated and stored (plus the value offset), no differences.
 template <class Map>
 __global__ void __launch_bounds__(256) k_value_build(LutView out, void* data, shm_source src, const __grid_constant__ Map map)
 {
-    __shared__ float bump[MAX_BUMPS_SMEM][5];
+    __shared__ BumpSmem bump;
     int tile;
     const int g = map_block(map, tile), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
@@ -431,24 +460,10 @@ __global__ void __launch_bounds__(256) k_value_build(LutView out, void* data, sh
         for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
             const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
             __syncthreads();
-            for (int e = tid; e < nb; e += 256) {
-                bump[e][0] = __ldg(src.mu + 3 * (bc + e));
-                bump[e][1] = __ldg(src.mu + 3 * (bc + e) + 1);
-                bump[e][2] = __ldg(src.mu + 3 * (bc + e) + 2);
-                bump[e][3] = __ldg(src.amp + bc + e);
-                const float wd = __ldg(src.width + bc + e);
-                bump[e][4] = -0.5f / (wd * wd);
-            }
+            stage_bumps(bump, src, bc, nb);
             __syncthreads();
-            for (int r = 0; r < 2; ++r) {
-                if (!live[r]) continue;
-                float sum = acc[r];
-                for (int q = 0; q < nb; ++q) {
-                    const float dx = w[r].x - bump[q][0], dy = w[r].y - bump[q][1], dz = w[r].z - bump[q][2];
-                    sum = fmaf(bump[q][3], expf((dx * dx + dy * dy + dz * dz) * bump[q][4]), sum);
-                }
-                acc[r] = sum;
-            }
+            for (int r = 0; r < 2; ++r)
+                if (live[r]) acc[r] = bump_sum(bump, nb, w[r], acc[r]);
         }
     }
     for (int r = 0; r < 2; ++r) {
@@ -473,7 +488,7 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                                                  const __grid_constant__ Map map)
 {
     extern __shared__ float Sf[];  // [T+2][T+2]
-    __shared__ float bump[MAX_BUMPS_SMEM][5];
+    __shared__ BumpSmem bump;
     int region;
     const int g = map_block(map, region), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
@@ -512,24 +527,9 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
         for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
             const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
             __syncthreads();
-            for (int e = tid; e < nb; e += 256) {
-                bump[e][0] = __ldg(src.mu + 3 * (bc + e));
-                bump[e][1] = __ldg(src.mu + 3 * (bc + e) + 1);
-                bump[e][2] = __ldg(src.mu + 3 * (bc + e) + 2);
-                bump[e][3] = __ldg(src.amp + bc + e);
-                const float wd = __ldg(src.width + bc + e);
-                bump[e][4] = -0.5f / (wd * wd);
-            }
+            stage_bumps(bump, src, bc, nb);
             __syncthreads();
-            for (int e = tid; e < Si * Sj; e += 256) {
-                const Vec3 w = dir(i0 + e % Si, j0 + e / Si);
-                float sum = Sf[e];
-                for (int q = 0; q < nb; ++q) {
-                    const float dx = w.x - bump[q][0], dy = w.y - bump[q][1], dz = w.z - bump[q][2];
-                    sum = fmaf(bump[q][3], expf((dx * dx + dy * dy + dz * dz) * bump[q][4]), sum);
-                }
-                Sf[e] = sum;
-            }
+            for (int e = tid; e < Si * Sj; e += 256) Sf[e] = bump_sum(bump, nb, dir(i0 + e % Si, j0 + e / Si), Sf[e]);
         }
     }
     __syncthreads();
