@@ -194,6 +194,7 @@ class GlyphField:
         self.dtype, self.layout = args.dtype_id, args.layout_id
         self.engine = args.engine
         self.e2e_chunks_n, self.e2e_streams_n = args.e2e_chunks, args.e2e_streams
+        self.e2e_mode_arg = args.e2e_mode
         self.seed = 20063 + 1 + 1000 * rank
         import shm_inputs as I
         self.c_host = I.sh_coeffs(self.G, self.L, self.seed).astype(np.float32)
@@ -239,9 +240,22 @@ class GlyphField:
         return self.Q
 
     def e2e_step(self, host_out):
-        """Public API from pinned host buffers, pipelined over glyph chunks on two streams: per chunk
-        H2D of its directions and coefficients, bake, query, D2H of its outputs, so that the copy
-        engines and the kernels of neighbouring chunks overlap."""
+        if self.e2e_mode == "zero_copy":
+            return self.e2e_step_zero_copy(host_out)
+        return self.e2e_step_pipeline(host_out)
+
+    def e2e_step_zero_copy(self, host_out):
+        """Public API on page-locked host buffers: the coefficients are copied to the device (5 MB),
+        the bake runs, and the query reads the directions from host memory and writes R, grad and
+        normal into host memory itself, over the host link, with no staging copies."""
+        self.coeffs.copy_(self.c_pinned, non_blocking=True)
+        self.S.build_lut(self.lut, self.src, ws=self.ws)
+        self.S.query(self.lut, self.dirs_host, seg=self.seg, out=host_out)
+
+    def e2e_step_pipeline(self, host_out):
+        """Public API from pinned host buffers, pipelined over glyph chunks on several streams: per
+        chunk H2D of its directions and coefficients, bake, query, D2H of its outputs, so that the
+        copy engines and the kernels of neighbouring chunks overlap."""
         torch, S = self.torch, self.S
         main = torch.cuda.current_stream()
         for st in self.e2e_streams:
@@ -260,13 +274,16 @@ class GlyphField:
         for st in self.e2e_streams:
             main.wait_stream(st)
 
-    def e2e_setup(self):
+    def e2e_setup(self, mode=None):
+        self.e2e_mode = mode or self.e2e_mode_arg
         chunks, streams = self.e2e_chunks_n, self.e2e_streams_n
         torch, S = self.torch, self.S
         self.c_pinned = torch.from_numpy(self.c_host).pin_memory()
         host_out = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in self.out.items()}
         h2d = self.dirs.numel() * 4 + self.coeffs.numel() * 4
         d2h = sum(v.numel() * 4 for v in self.out.values())
+        if self.e2e_mode == "zero_copy":
+            return host_out, h2d, d2h
         self.e2e_streams = [torch.cuda.Stream() for _ in range(streams)]
         per_glyph = S.records_per_glyph(self.N, self.layout) * S.record_bytes(self.dtype, self.layout)
         elem = self.lut.data.element_size()
@@ -353,9 +370,75 @@ class GlyphField:
             del L16, o16
         del dl
         ex["write_ceiling"] = self.write_ceiling(torch, timeit, n)
+        ex["e2e_modes"] = self.e2e_mode_extras(torch)
         ex["recon"] = self.recon_extras(S, torch, timeit, n, fwd)
         ex["cuda_graph"] = self.graph_extras(S, torch, timeit, n)
         return ex
+
+    def e2e_mode_extras(self, torch):
+        """End to end (public API, page-locked host buffers) in both forms: kernels reading and
+        writing the host buffers directly, and chunked staging copies overlapped with the kernels."""
+        res = {}
+        keep = self.e2e_mode
+        for mode in ("zero_copy", "copy_pipeline"):
+            host_out, h2d, d2h = self.e2e_setup(mode)
+            for _ in range(2):
+                self.e2e_step(host_out)
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(3):
+                self.e2e_step(host_out)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            res[mode] = {"ms_per_step": round(ms, 3), "queries_per_s": self.Q / (ms * 1e-3),
+                         "host_link_GBps": round((h2d + d2h) / (ms * 1e-3) / 1e9, 1)}
+            if mode == "copy_pipeline":
+                res["host_link_ceiling"] = self.host_link_ceiling(torch, host_out)
+                res["copy_pipeline"]["frac_of_host_link_ceiling"] = round(
+                    res["host_link_ceiling"]["both_ms"] / ms, 3)
+            del host_out
+        self.e2e_mode = keep
+        return res
+
+    def host_link_ceiling(self, torch, host_out):
+        """Plain copies of the step's bytes between page-locked host memory and the device: the
+        directions host to device, the outputs device to host, each alone and both at once on two
+        streams (torch copies, the copy engines)."""
+        st = [torch.cuda.Stream(), torch.cuda.Stream()]
+
+        def h2d():
+            with torch.cuda.stream(st[0]):
+                self.dirs.copy_(self.dirs_host, non_blocking=True)
+
+        def d2h():
+            with torch.cuda.stream(st[1]):
+                for k in ("R", "grad", "normal"):
+                    host_out[k].copy_(self.out[k], non_blocking=True)
+
+        def timed(*fns):
+            main = torch.cuda.current_stream()
+            for s_ in st:
+                s_.wait_stream(main)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main)
+            for s_ in st:
+                s_.wait_event(e0)
+            for _ in range(3):
+                for fn in fns:
+                    fn()
+            for s_ in st:
+                main.wait_stream(s_)
+            e1.record(main)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 3
+        bi, bo = self.dirs.numel() * 4, sum(v.numel() * 4 for v in self.out.values())
+        t_in, t_out, t_both = timed(h2d), timed(d2h), timed(h2d, d2h)
+        return {"h2d_ms": round(t_in, 3), "h2d_GBps": round(bi / (t_in * 1e-3) / 1e9, 1),
+                "d2h_ms": round(t_out, 3), "d2h_GBps": round(bo / (t_out * 1e-3) / 1e9, 1),
+                "both_ms": round(t_both, 3), "both_GBps": round((bi + bo) / (t_both * 1e-3) / 1e9, 1)}
 
     def write_ceiling(self, torch, timeit, n):
         """Write-only ceiling for the bake, which reads almost nothing and writes the table: a
@@ -1167,7 +1250,9 @@ def run_gpu(args):
             "config": dict(work.config, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": world * work.units_per_step() / (e2e_ms * 1e-3), "unit": work.unit,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "host_link_GBps": round((h2d + d2h) / (e2e_ms * 1e-3) / 1e9, 1),
+                    "mode": getattr(work, "e2e_mode", "copies")},
             "gpu_launches": work.launches_per_step * args.steps, "clocks": clk, "kernels": kernels,
             "extras": extras}
     if rank == 0:
@@ -1198,6 +1283,8 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-chunks", type=int, default=16,
                     help="glyph field end to end: glyph chunks per step (copies and kernels of neighbouring chunks overlap)")
     ap.add_argument("--e2e-streams", type=int, default=3, help="glyph field end to end: streams the chunks rotate over")
+    ap.add_argument("--e2e-mode", choices=["zero_copy", "copy_pipeline"], default="copy_pipeline",
+                    help="glyph field end to end: kernels on page-locked host buffers, or chunked copies")
     args = ap.parse_args(argv)
     args.dtype_id = {"f32": 0, "f16": 1, "bf16": 2}[args.dtype]
     args.layout_id = {"texel": 0, "cell": 1}[args.layout]

@@ -12,6 +12,12 @@
  *     The library allocates no device memory and keeps no state between calls, except the
  *     static workspace of shm_raycast_noalloc and the launch-shape table of shm_tune_query
  *     (both described there).
+ *   - Per-query buffers of shm_query, shm_query_recon, shm_tune_query, shm_query_backward and
+ *     shm_fit_backward (directions, glyph ids, segments, outputs, upstream gradients, targets,
+ *     loss, dev_status) may instead be page-locked host memory (cudaHostAlloc / cudaHostRegister):
+ *     the kernels read and write it directly over the host link through its device alias, so no
+ *     staging copy is needed.  Pageable host memory there gives SHM_ERR_INVALID_ARG.  Tables,
+ *     coefficients and workspaces are device memory.
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  *     The returned status covers host-side argument validation and launch errors only.
  *   - Conditions found on the device never trap: they are OR-ed into *dev_status (device

@@ -127,9 +127,25 @@ def _ptr(t: Optional[torch.Tensor]):
     return C.c_void_p(t.data_ptr())
 
 
+def _io_ptr(t: Optional[torch.Tensor]):
+    """Pointer of a per-query buffer: device memory, or host memory handed to the library, which
+    accepts page-locked host buffers and refuses pageable ones (SHM_ERR_INVALID_ARG)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def _io_empty(shape, dtype, like: torch.Tensor) -> torch.Tensor:
+    """An output buffer next to `like`: on its device, or page-locked host memory when `like` is
+    page-locked host memory (the kernels write it directly)."""
+    if like.device.type == "cpu":
+        return torch.empty(shape, dtype=dtype, pin_memory=True)
+    return torch.empty(shape, dtype=dtype, device=like.device)
 
 
 def _need(t: Optional[torch.Tensor], dtype, shape=None, name="tensor"):
@@ -241,15 +257,14 @@ def query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.T
     Q = dirs.shape[0]
     _need(glyph, torch.int32, (Q,), "glyph")
     _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
-    dev = dirs.device
     out = {} if out is None else out
     shapes = {"R": (Q,), "grad": (Q, 3), "normal": (Q, 3), "chart": (Q, 2), "fij": (Q, 3)}
     for k in want:
         if k not in out:
-            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "fij" else torch.float32, device=dev)
-    st = lib().shm_query(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(out.get("R")),
-                         _ptr(out.get("grad")), _ptr(out.get("normal")), _ptr(out.get("chart")),
-                         _ptr(out.get("fij")), _ptr(dev_status), _stream(stream))
+            out[k] = _io_empty(shapes[k], torch.int32 if k == "fij" else torch.float32, dirs)
+    st = lib().shm_query(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg), _io_ptr(out.get("R")),
+                         _io_ptr(out.get("grad")), _io_ptr(out.get("normal")), _io_ptr(out.get("chart")),
+                         _io_ptr(out.get("fij")), _io_ptr(dev_status), _stream(stream))
     _check(st, "shm_query")
     return out
 
@@ -263,12 +278,11 @@ def tune_query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: to
     Q = dirs.shape[0]
     _need(glyph, torch.int32, (Q,), "glyph")
     _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
-    out = {k: torch.empty(s, dtype=torch.float32, device=dirs.device)
-           for k, s in (("R", (Q,)), ("grad", (Q, 3)), ("normal", (Q, 3)))}
+    out = {k: _io_empty(s, torch.float32, dirs) for k, s in (("R", (Q,)), ("grad", (Q, 3)), ("normal", (Q, 3)))}
     chosen = C.c_int32(-1)
     times = (C.c_float * 4)()
-    _check(lib().shm_tune_query(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(out["R"]),
-                                _ptr(out["grad"]), _ptr(out["normal"]), int(reps), C.byref(chosen), times,
+    _check(lib().shm_tune_query(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg), _io_ptr(out["R"]),
+                                _io_ptr(out["grad"]), _io_ptr(out["normal"]), int(reps), C.byref(chosen), times,
                                 _stream(stream)), "shm_tune_query")
     return {"chosen": chosen.value, "times_ms": [round(float(t), 5) for t in times]}
 
@@ -284,15 +298,15 @@ def query_recon(lut: Lut, method: int, dirs: torch.Tensor, glyph: torch.Tensor =
     Q = dirs.shape[0]
     _need(glyph, torch.int32, (Q,), "glyph")
     _need(seg, torch.int64, (lut.n_glyphs + 1,), "seg")
-    dev = dirs.device
     out = {} if out is None else out
     shapes = {"R": (Q,), "grad": (Q, 3), "normal": (Q, 3), "chart": (Q, 2), "fij": (Q, 3)}
     for k in want:
         if k not in out:
-            out[k] = torch.empty(shapes[k], dtype=torch.int32 if k == "fij" else torch.float32, device=dev)
-    st = lib().shm_query_recon(C.byref(lut.c()), int(method), Q, _ptr(dirs), _ptr(glyph), _ptr(seg),
-                               _ptr(out.get("R")), _ptr(out.get("grad")), _ptr(out.get("normal")),
-                               _ptr(out.get("chart")), _ptr(out.get("fij")), _ptr(dev_status), _stream(stream))
+            out[k] = _io_empty(shapes[k], torch.int32 if k == "fij" else torch.float32, dirs)
+    st = lib().shm_query_recon(C.byref(lut.c()), int(method), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg),
+                               _io_ptr(out.get("R")), _io_ptr(out.get("grad")), _io_ptr(out.get("normal")),
+                               _io_ptr(out.get("chart")), _io_ptr(out.get("fij")), _io_ptr(dev_status),
+                               _stream(stream))
     _check(st, "shm_query_recon")
     return out
 
@@ -402,9 +416,10 @@ def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None,
     Q = dirs.shape[0]
     for t, nm in ((gR, "gR"), (ggrad, "ggrad"), (gnormal, "gnormal")):
         _need(t, torch.float32, name=nm)
-    ddirs = torch.empty((Q, 3), dtype=torch.float32, device=dirs.device) if want_ddirs else None
-    st = lib().shm_query_backward(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(gR), _ptr(ggrad),
-                                  _ptr(gnormal), C.byref(dlut.c()), _ptr(ddirs), _ptr(dev_status), _stream(stream))
+    ddirs = _io_empty((Q, 3), torch.float32, dirs) if want_ddirs else None
+    st = lib().shm_query_backward(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg), _io_ptr(gR),
+                                  _io_ptr(ggrad), _io_ptr(gnormal), C.byref(dlut.c()), _io_ptr(ddirs),
+                                  _io_ptr(dev_status), _stream(stream))
     _check(st, "shm_query_backward")
     return ddirs
 
@@ -425,9 +440,9 @@ def fit_backward(lut: Lut, dirs: torch.Tensor, R_target: torch.Tensor, n_target:
     Q = dirs.shape[0]
     _need(R_target, torch.float32, (Q,), "R_target")
     _need(n_target, torch.float32, (Q, 3), "n_target")
-    st = lib().shm_fit_backward(C.byref(lut.c()), Q, _ptr(dirs), _ptr(glyph), _ptr(seg), _ptr(R_target),
-                                _ptr(n_target), float(w_value), float(w_normal), C.byref(dlut.c()), _ptr(loss),
-                                _ptr(dev_status), _stream(stream))
+    st = lib().shm_fit_backward(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg), _io_ptr(R_target),
+                                _io_ptr(n_target), float(w_value), float(w_normal), C.byref(dlut.c()),
+                                _io_ptr(loss), _io_ptr(dev_status), _stream(stream))
     _check(st, "shm_fit_backward")
 
 

@@ -55,6 +55,46 @@ static LutView view(const shm_lut* L)
 
 static shm_status map_cuda(cudaError_t e) { return e == cudaSuccess ? SHM_OK : SHM_ERR_CUDA; }
 
+// Per-query input and output buffers may live in device memory or in page-locked host memory
+// (cudaHostAlloc / cudaHostRegister): the kernels then read and write the host buffer directly over
+// the host link, through the pointer's device alias.  Pageable host memory is rejected, so that no
+// kernel ever dereferences an address the device cannot reach.
+template <class T>
+static shm_status io_ptr(T*& p)
+{
+    if (!p) return SHM_OK;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, (const void*)p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SHM_ERR_INVALID_ARG;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return SHM_OK;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        p = static_cast<T*>(at.devicePointer);
+        return SHM_OK;
+    }
+    return SHM_ERR_INVALID_ARG;
+}
+
+static shm_status resolve_io(QueryArgs& a)
+{
+    shm_status st = SHM_OK;
+    for (shm_status e : {io_ptr(a.dirs), io_ptr(a.glyph), io_ptr(a.seg), io_ptr(a.R), io_ptr(a.grad),
+                         io_ptr(a.normal), io_ptr(a.chart), io_ptr(a.fij), io_ptr(a.dev_status)})
+        if (e != SHM_OK) st = e;
+    return st;
+}
+
+static shm_status resolve_io(BackwardArgs& a)
+{
+    shm_status st = SHM_OK;
+    for (shm_status e : {io_ptr(a.dirs), io_ptr(a.glyph), io_ptr(a.seg), io_ptr(a.gR), io_ptr(a.ggrad),
+                         io_ptr(a.gnormal), io_ptr(a.ddirs), io_ptr(a.dev_status), io_ptr(a.R_target),
+                         io_ptr(a.n_target), io_ptr(a.loss)})
+        if (e != SHM_OK) st = e;
+    return st;
+}
+
 // Glyph resolutions for the launch grids: uniform N, or the per-glyph array read from the device
 // (one synchronous copy on `stream`; callers with N_uniform avoid it).
 static Sizes sizes_of(const shm_lut* L, cudaStream_t s, shm_status* st, std::vector<int32_t>& buf)
@@ -132,6 +172,7 @@ shm_status shm_query(const shm_lut* lut, int64_t Q, const float* dirs, const int
     a.chart = chart;
     a.fij = fij;
     a.dev_status = dev_status;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
     return map_cuda(launch_query_fwd(a, (cudaStream_t)stream));
 }
 
@@ -155,6 +196,7 @@ shm_status shm_tune_query(const shm_lut* lut, int64_t Q, const float* dirs, cons
     a.chart = nullptr;
     a.fij = nullptr;
     a.dev_status = nullptr;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = query_shapes(a);
     cudaEvent_t e0, e1;
@@ -212,6 +254,7 @@ shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const 
     a.chart = chart;
     a.fij = fij;
     a.dev_status = dev_status;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
     return map_cuda(launch_query_recon(a, method, (cudaStream_t)stream));
 }
 
@@ -380,6 +423,7 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, 
     a.R_target = a.n_target = nullptr;
     a.w_value = a.w_normal = 0.0f;
     a.loss = nullptr;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
     return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
 }
 
@@ -412,6 +456,7 @@ shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, co
     a.w_value = w_value;
     a.w_normal = w_normal;
     a.loss = loss;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
     return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
 }
 
