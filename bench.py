@@ -352,8 +352,12 @@ class GlyphField:
         fwd = timeit(lambda: S.query(self.lut, self.dirs, seg=self.seg, out=self.out), n)
         bwd = timeit(lambda: S.query_backward(self.lut, self.dirs, dl, gR=gR, ggrad=gG, gnormal=gN, seg=self.seg,
                                               want_ddirs=True), n)
+        bwd_det = timeit(lambda: S.query_backward(self.lut, self.dirs, dl, gR=gR, ggrad=gG, gnormal=gN, seg=self.seg,
+                                                  want_ddirs=True, deterministic=True), n)
         ex["fwd_bwd"] = {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4), "fwd_plus_bwd_over_fwd": round((fwd + bwd) / fwd, 3),
-                         "note": "backward = recompute + 4 float4 atomics per query into a float32 texel table + d/ddirs"}
+                         "bwd_deterministic_ms": round(bwd_det, 4),
+                         "note": "backward = recompute + 4 float4 atomics per query into a float32 texel table + d/ddirs; "
+                                 "deterministic = per-glyph CTA, chunks sorted by cell, per-cell sums added in a fixed order"}
         ref = {k: v.clone() for k, v in self.out.items()}
         for name, dt in (("bf16", S.SHM_BF16), ("f16", S.SHM_F16)):
             r0 = torch.full((self.G,), 0.7, dtype=torch.float32, device="cuda")

@@ -248,15 +248,23 @@ shm_status shm_build_mip(const shm_lut* fine, const shm_lut* coarse, int32_t* de
 
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 
+/* Flags of shm_query_backward. */
+#define SHM_BWD_DETERMINISTIC 1u /* fixed summation order: dlut bit-identical from run to run */
+
 /* Reverse mode of shm_query.  Upstream gradients gR [Q], ggrad [Q][3], gnormal [Q][3] (each
  * may be NULL = 0).  Accumulates (+=) dL/d(stored record) into dlut, a float32 TEXEL-layout
- * table with the same glyphs and resolutions as lut (any lut dtype/layout is read), and
- * writes (=) dL/d(dirs) into ddirs [Q][3] if not NULL.  Atomic accumulation: the summation
- * order, hence the last bits of dlut, may vary from run to run. */
+ * table with the same glyphs and resolutions as lut (any lut dtype/layout is read; a mismatch
+ * gives SHM_ERR_INVALID_ARG), and writes (=) dL/d(dirs) into ddirs [Q][3] if not NULL.
+ * flags = 0: atomic accumulation; the summation order, hence the last bits of dlut, may vary from
+ * run to run.  flags = SHM_BWD_DETERMINISTIC: one CTA per glyph sorts each chunk of the glyph's
+ * queries by cell and adds the per-cell sums in a fixed order, so dlut is bit-identical from run
+ * to run and for any launch shape; needs CSR segments (glyph = NULL, seg != NULL, else
+ * SHM_ERR_UNSUPPORTED) and parallelises over glyphs, so it suits many-glyph batches.  Other flag
+ * bits: SHM_ERR_INVALID_ARG. */
 shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
                               const int32_t* glyph, const int64_t* seg, const float* gR,
                               const float* ggrad, const float* gnormal, const shm_lut* dlut,
-                              float* ddirs, int32_t* dev_status, shm_stream stream);
+                              float* ddirs, uint32_t flags, int32_t* dev_status, shm_stream stream);
 
 /* Reverse mode of the SH bake: dcoeffs[g][k] (=) sum over texels and channels of
  * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L). */

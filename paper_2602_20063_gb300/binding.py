@@ -21,6 +21,7 @@ SHM_LAYOUT_TEXEL, SHM_LAYOUT_CELL, SHM_LAYOUT_VALUE = 0, 1, 2
 SHM_RECON_NEAREST, SHM_RECON_BILINEAR, SHM_RECON_BICUBIC, SHM_RECON_FAST_BICUBIC = 0, 1, 2, 3
 SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM = 0, 1, 2, 3
 SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT = 1, 2, 4
+SHM_BWD_DETERMINISTIC = 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error", 5: "timeout"}
 
 DTYPES = {SHM_F32: torch.float32, SHM_F16: torch.float16, SHM_BF16: torch.bfloat16}
@@ -78,7 +79,7 @@ _SIGS = {
     "shm_pack_lut": (C.c_int, [_VP, _VP, _VP]),
     "shm_lut_bounds": (C.c_int, [_VP, _VP, _VP]),
     "shm_build_mip": (C.c_int, [_VP, _VP, _VP, _VP]),
-    "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP, _VP]),
     "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
     "shm_fit_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
     "shm_adam_step": (C.c_int, [_VP, _VP, _VP, _VP, _I64, C.c_float, C.c_float, C.c_float, C.c_float, _I32, _I32, _VP]),
@@ -410,8 +411,9 @@ def mip_chain(fine: Lut, levels: int, dtype: int = None, layout: int = None, str
 
 # ------------------------------------------------------------------------------------------- adjoint
 def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None, gnormal=None, glyph=None, seg=None,
-                   want_ddirs=True, dev_status=None, stream=None):
-    """shm_query_backward: accumulates into dlut (float32 texel layout); returns ddirs or None."""
+                   want_ddirs=True, dev_status=None, stream=None, deterministic=False):
+    """shm_query_backward: accumulates into dlut (float32 texel layout); returns ddirs or None.
+    deterministic=True (SHM_BWD_DETERMINISTIC, segments only): dlut bit-identical run to run."""
     _need(dirs, torch.float32, name="dirs")
     Q = dirs.shape[0]
     for t, nm in ((gR, "gR"), (ggrad, "ggrad"), (gnormal, "gnormal")):
@@ -419,7 +421,8 @@ def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None,
     ddirs = _io_empty((Q, 3), torch.float32, dirs) if want_ddirs else None
     st = lib().shm_query_backward(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(glyph), _io_ptr(seg), _io_ptr(gR),
                                   _io_ptr(ggrad), _io_ptr(gnormal), C.byref(dlut.c()), _io_ptr(ddirs),
-                                  _io_ptr(dev_status), _stream(stream))
+                                  C.c_uint32(SHM_BWD_DETERMINISTIC if deterministic else 0), _io_ptr(dev_status),
+                                  _stream(stream))
     _check(st, "shm_query_backward")
     return ddirs
 

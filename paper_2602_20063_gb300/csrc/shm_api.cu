@@ -76,6 +76,21 @@ static shm_status io_ptr(T*& p)
     return SHM_ERR_INVALID_ARG;
 }
 
+// The gradient table of a reverse pass must have the table's glyphs and resolutions (its records
+// are addressed with the table's N).  Per-glyph resolutions are compared on the host.
+static shm_status same_resolutions(const shm_lut* a, const shm_lut* b, cudaStream_t s)
+{
+    if (a->n_glyphs != b->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if (a->N_uniform > 0 || b->N_uniform > 0) return a->N_uniform == b->N_uniform ? SHM_OK : SHM_ERR_INVALID_ARG;
+    if (a->N == b->N) return SHM_OK;
+    std::vector<int32_t> na(a->n_glyphs), nb(b->n_glyphs);
+    if (cudaMemcpyAsync(na.data(), a->N, sizeof(int32_t) * na.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(nb.data(), b->N, sizeof(int32_t) * nb.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SHM_ERR_CUDA;
+    return na == nb ? SHM_OK : SHM_ERR_INVALID_ARG;
+}
+
 static shm_status resolve_io(QueryArgs& a)
 {
     shm_status st = SHM_OK;
@@ -396,7 +411,8 @@ shm_status shm_build_mip(const shm_lut* fine, const shm_lut* coarse, int32_t* de
 
 shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
                               const int64_t* seg, const float* gR, const float* ggrad, const float* gnormal,
-                              const shm_lut* dlut, float* ddirs, int32_t* dev_status, shm_stream stream)
+                              const shm_lut* dlut, float* ddirs, uint32_t flags, int32_t* dev_status,
+                              shm_stream stream)
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
@@ -404,8 +420,11 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, 
     st = check_lut(dlut);
     if (st != SHM_OK) return st;
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
-    if (dlut->n_glyphs != lut->n_glyphs) return SHM_ERR_INVALID_ARG;
+    if ((flags & ~(uint32_t)SHM_BWD_DETERMINISTIC) != 0) return SHM_ERR_INVALID_ARG;
     if (Q < 0 || (Q > 0 && !dirs)) return SHM_ERR_INVALID_ARG;
+    const bool det = (flags & SHM_BWD_DETERMINISTIC) != 0;
+    if (det && (glyph || !seg)) return SHM_ERR_UNSUPPORTED;
+    if ((st = same_resolutions(lut, dlut, (cudaStream_t)stream)) != SHM_OK) return st;
     BackwardArgs a;
     a.L = view(lut);
     a.D = view(dlut);
@@ -424,7 +443,7 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs, 
     a.w_value = a.w_normal = 0.0f;
     a.loss = nullptr;
     if ((st = resolve_io(a)) != SHM_OK) return st;
-    return map_cuda(launch_query_bwd(a, (cudaStream_t)stream));
+    return map_cuda(det ? launch_query_bwd_det(a, (cudaStream_t)stream) : launch_query_bwd(a, (cudaStream_t)stream));
 }
 
 shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, const int32_t* glyph,
@@ -437,8 +456,8 @@ shm_status shm_fit_backward(const shm_lut* lut, int64_t Q, const float* dirs, co
     st = check_lut(dlut);
     if (st != SHM_OK) return st;
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL) return SHM_ERR_UNSUPPORTED;
-    if (dlut->n_glyphs != lut->n_glyphs) return SHM_ERR_INVALID_ARG;
     if (Q < 0 || (Q > 0 && (!dirs || !R_target || !n_target))) return SHM_ERR_INVALID_ARG;
+    if ((st = same_resolutions(lut, dlut, (cudaStream_t)stream)) != SHM_OK) return st;
     BackwardArgs a;
     a.L = view(lut);
     a.D = view(dlut);

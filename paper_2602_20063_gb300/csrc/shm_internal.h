@@ -127,6 +127,7 @@ struct BackwardArgs {
 int sm_count();
 
 cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s);
+cudaError_t launch_query_bwd_det(const BackwardArgs& a, cudaStream_t s);
 // Glyph tables up to this size are staged whole in shared memory by the segment query (two CTAs
 // of 512 threads per SM: (232,448 - 2 x 1 KB reserved) / 2 minus the barrier block).
 constexpr int64_t STAGED_TABLE_MAX_BYTES = 114688;

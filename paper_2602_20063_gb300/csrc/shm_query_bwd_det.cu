@@ -1,0 +1,254 @@
+// Deterministic reverse pass of the query (SHM_BWD_DETERMINISTIC; not in the paper): dL/dtable comes
+// out bit-identical from run to run and independent of the launch shape, by a segmented reduction in
+// a fixed order instead of atomic accumulation.
+//
+// Needs per-glyph query segments: one CTA owns a glyph (and so its dL/dtable slab) and walks the
+// glyph's queries in chunks of DBLOCK.  Per chunk:
+//   1. every thread runs the reverse math of its query (shm_bwd.cuh), writes d/ddirs, and keeps the
+//      cell (record index of corner (0,0)) as a sort key and (s, t, g_r, g_rs, g_rt) in shared memory;
+//   2. a bitonic sort of (cell, query) keys groups the chunk's queries by cell, in query order
+//      (keys in registers; partners within a warp by shuffles, across warps through shared memory);
+//   3. the first thread of each cell's run sums the corner weights of the run's queries in that order;
+//   4. four passes, one per corner (aa, bb), add those sums to the slab with plain loads and stores:
+//      within one pass distinct cells write distinct records, and the passes are separated by CTA
+//      barriers, so every record receives its contributions in a fixed order.
+// Chunks run in order inside the CTA, glyphs are disjoint, so the whole result is fixed.  Small
+// uniform texel tables are staged in shared memory as in the atomic staged pass.
+#include "shm_bwd.cuh"
+#include "shm_stage.cuh"
+
+namespace shm {
+
+namespace {
+
+constexpr int DBLOCK = 1024;
+constexpr int DBITS = 10;  // log2(DBLOCK): query slot in the low bits of the sort key
+constexpr uint64_t NO_KEY = ~0ull;
+
+// Shared memory after the (optional) staged table: two key buffers [DBLOCK] u64, then the payload
+// [5][DBLOCK] f32.
+constexpr uint32_t DET_SMEM_FIXED = 2 * DBLOCK * 8 + 5 * DBLOCK * 4;
+
+struct DetEmit {
+    uint64_t key;
+    float* pay;  // [5][DBLOCK]: s, t, g_r, g_rs, g_rt
+    int slot;
+    __device__ __forceinline__ void operator()(int rec, const Herm2&, const Herm2&, float s, float t, float g_r,
+                                               float g_rs, float g_rt)
+    {
+        key = ((uint64_t)rec << DBITS) | (uint64_t)slot;
+        pay[slot] = s;
+        pay[DBLOCK + slot] = t;
+        pay[2 * DBLOCK + slot] = g_r;
+        pay[3 * DBLOCK + slot] = g_rs;
+        pay[4 * DBLOCK + slot] = g_rt;
+    }
+};
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
+{
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Ascending bitonic sort of the DBLOCK keys held one per thread (thread tid holds position tid).
+// Compare-exchange partners tid ^ j: by shuffles for j < 32, through shared memory otherwise, with
+// two buffers used in turn so that one barrier per shared stage suffices.  Returns the key at
+// position tid; the sorted keys are also left in `out` (one of the two buffers) after a barrier.
+__device__ __forceinline__ uint64_t bitonic_sort(uint64_t x, uint64_t* buf0, uint64_t* buf1, uint64_t*& out, int tid)
+{
+    int flip = 0;
+    for (int k = 2; k <= DBLOCK; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t y;
+            if (j >= 32) {
+                uint64_t* b = flip ? buf1 : buf0;
+                flip ^= 1;
+                b[tid] = x;
+                __syncthreads();
+                y = b[tid ^ j];
+            } else {
+                y = shfl_xor_u64(x, j);
+            }
+            const bool up = (tid & k) == 0, lower = (tid & j) == 0;
+            x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
+        }
+    // the buffer not written by the last shared stage is free: every thread has passed that stage's barrier
+    out = flip ? buf1 : buf0;
+    out[tid] = x;
+    __syncthreads();
+    return x;
+}
+
+template <int DT, int LAYOUT, bool STAGED>
+__global__ void __launch_bounds__(DBLOCK, 1) k_query_bwd_det(BackwardArgs a, uint32_t table_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem);
+    const unsigned char* table = smem + stage::TABLE_OFFSET;
+    unsigned char* fixed = smem + (STAGED ? stage::TABLE_OFFSET + table_bytes : 0);
+    uint64_t* kbuf0 = reinterpret_cast<uint64_t*>(fixed);
+    uint64_t* kbuf1 = kbuf0 + DBLOCK;
+    float* pay = reinterpret_cast<float*>(fixed + 2 * DBLOCK * 8);
+    const int tid = threadIdx.x;
+    const int G = a.L.n_glyphs;
+    uint32_t status = 0;
+    float loss_unused = 0.0f;
+    const float qnan = __int_as_float(0x7fc00000);
+    {
+        // queries outside every segment: NaN d/ddirs and SHM_DEV_BOUNDS
+        const int64_t lo = min(max(__ldg(a.seg), (int64_t)0), a.Q);
+        const int64_t hi = min(max(__ldg(a.seg + G), lo), a.Q);
+        const int64_t stride = (int64_t)gridDim.x * DBLOCK;
+        for (int part = 0; part < 2; ++part) {
+            const int64_t b = part ? hi : 0, e = part ? a.Q : lo;
+            for (int64_t q = b + (int64_t)blockIdx.x * DBLOCK + tid; q < e; q += stride) {
+                status |= SHM_DEV_BOUNDS;
+                if (a.ddirs) { a.ddirs[3 * q] = qnan; a.ddirs[3 * q + 1] = qnan; a.ddirs[3 * q + 2] = qnan; }
+            }
+        }
+    }
+    if (STAGED && tid == 0) {
+        stage::init(bar);
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const int64_t s0 = min(max(__ldg(a.seg + g), (int64_t)0), a.Q);
+        const int64_t s1 = min(max(__ldg(a.seg + g + 1), s0), a.Q);
+        if (s1 <= s0) continue;  // block-uniform
+        if (STAGED) {
+            if (tid == 0)
+                stage::issue(bar, bar + stage::TABLE_OFFSET,
+                             reinterpret_cast<const unsigned char*>(a.L.data) + (size_t)g * table_bytes, table_bytes);
+            if (!stage::bar_wait(bar, phase, stage::WAIT_NS)) s_abort = 1;
+            __syncthreads();
+            if (s_abort) {
+                status |= SHM_DEV_TIMEOUT;
+                if (tid == 0) stage::bar_wait(bar, phase, stage::DRAIN_NS);
+                break;
+            }
+            phase ^= 1;
+        }
+        const GlyphRef Gr = glyph_ref(a.L, g);
+        const int P = Gr.N + 2;
+        float4* dbase = reinterpret_cast<float4*>(a.dlut) + glyph_ref(a.D, g).base;
+        for (int64_t c0 = s0; c0 < s1; c0 += DBLOCK) {
+            // 1. reverse math per query; key and payload into shared memory
+            const int64_t q = c0 + tid;
+            DetEmit emit{NO_KEY, pay, tid};
+            if (q < s1) {
+                float3 dd = make_float3(qnan, qnan, qnan);
+                const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
+                Chart c;
+                if (chart_of(d0, d1, d2, c)) {
+                    if (STAGED) {
+                        auto fetch = [table, P](int f, int i, int j) { return stage::corners<DT>(table, P, f, i, j); };
+                        bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
+                    } else {
+                        auto fetch = [&a, &Gr](int f, int i, int j) {
+                            return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j);
+                        };
+                        bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
+                    }
+                } else {
+                    status |= SHM_DEV_NONFINITE;
+                }
+                if (a.ddirs) { a.ddirs[3 * q] = dd.x; a.ddirs[3 * q + 1] = dd.y; a.ddirs[3 * q + 2] = dd.z; }
+            }
+            // 2. group by cell, queries in order within a cell (the payload writes are ordered before
+            //    the reads of step 3 by the sort's barriers)
+            uint64_t* key;
+            const uint64_t k = bitonic_sort(emit.key, kbuf0, kbuf1, key, tid);
+            // 3. the first slot of each cell's run sums the run in query order
+            const uint64_t cell = k >> DBITS;
+            const bool head = (k != NO_KEY) && (tid == 0 || (key[tid - 1] >> DBITS) != cell);
+            float4 acc[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (head) {
+                for (int r = tid; r < DBLOCK; ++r) {
+                    const uint64_t kr = key[r];
+                    if (kr == NO_KEY || (kr >> DBITS) != cell) break;
+                    const int src = (int)(kr & (DBLOCK - 1));
+                    const Herm2 A = herm2(pay[src]), B = herm2(pay[DBLOCK + src]);
+                    float4 w[4];
+                    corner_weights(A, B, pay[2 * DBLOCK + src], pay[3 * DBLOCK + src], pay[4 * DBLOCK + src], w);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        acc[m].x += w[m].x;
+                        acc[m].y += w[m].y;
+                        acc[m].z += w[m].z;
+                        acc[m].w += w[m].w;
+                    }
+                }
+            }
+            // 4. one pass per corner: distinct cells touch distinct records within a pass
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (head) {
+                    float4* p = dbase + (int64_t)cell + (m >> 1) * P + (m & 1);
+                    float4 v = *p;
+                    v.x += acc[m].x;
+                    v.y += acc[m].y;
+                    v.z += acc[m].z;
+                    v.w += acc[m].w;
+                    *p = v;
+                }
+                __syncthreads();
+            }
+        }
+        if (STAGED) __syncthreads();  // every read of this table is done before the next copy lands
+    }
+    report_status(a.dev_status, status);
+}
+
+template <int DT, int LAYOUT, bool STAGED>
+cudaError_t launch_det_t(const BackwardArgs& a, uint32_t table_bytes, cudaStream_t s)
+{
+    const int smem = (STAGED ? stage::TABLE_OFFSET + (int)table_bytes : 0) + (int)DET_SMEM_FIXED;
+    static int configured = -1;
+    if (configured != smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_det<DT, LAYOUT, STAGED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int64_t blocks = (int64_t)sm_count();
+    if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
+    if (blocks < 1) blocks = 1;
+    k_query_bwd_det<DT, LAYOUT, STAGED><<<(unsigned)blocks, DBLOCK, smem, s>>>(a, table_bytes);
+    return cudaGetLastError();
+}
+
+template <int DT, int LAYOUT>
+cudaError_t launch_det_dl(const BackwardArgs& a, cudaStream_t s)
+{
+    if (LAYOUT == SHM_LAYOUT_TEXEL && a.L.N_uniform > 0) {
+        const int64_t P = (int64_t)a.L.N_uniform + 2;
+        const int64_t bytes = 6 * P * P * (DT == SHM_F32 ? 16 : 8);
+        if (bytes <= STAGED_TABLE_MAX_BYTES) return launch_det_t<DT, LAYOUT, true>(a, (uint32_t)bytes, s);
+    }
+    return launch_det_t<DT, LAYOUT, false>(a, 0, s);
+}
+
+}  // namespace
+
+cudaError_t launch_query_bwd_det(const BackwardArgs& a, cudaStream_t s)
+{
+    if (a.Q == 0) return cudaSuccess;
+    const int dt = a.L.dtype;
+    if (a.L.layout == SHM_LAYOUT_TEXEL) {
+        if (dt == SHM_F32) return launch_det_dl<SHM_F32, SHM_LAYOUT_TEXEL>(a, s);
+        if (dt == SHM_F16) return launch_det_dl<SHM_F16, SHM_LAYOUT_TEXEL>(a, s);
+        return launch_det_dl<SHM_BF16, SHM_LAYOUT_TEXEL>(a, s);
+    }
+    if (dt == SHM_F32) return launch_det_dl<SHM_F32, SHM_LAYOUT_CELL>(a, s);
+    if (dt == SHM_F16) return launch_det_dl<SHM_F16, SHM_LAYOUT_CELL>(a, s);
+    return launch_det_dl<SHM_BF16, SHM_LAYOUT_CELL>(a, s);
+}
+
+}  // namespace shm

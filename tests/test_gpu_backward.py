@@ -144,3 +144,78 @@ def test_segments_and_glyph_ids_agree_with_oracle(S, dtype):
         got = dl.data.view(-1, 4).double().cpu().numpy() - base
         for ch in range(4):
             assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * np.abs(dref[:, ch]).max() + 4e-7 * np.abs(base[:, ch]).max(), ch
+
+
+def _det_case(S, N, G, counts, dtype, layout, seed):
+    luts = [O.bake_sh(N, 5, I.sh_coeffs(1, 5, seed + g)[0] + np.eye(1, 36, 0)[0] * 2.0) for g in range(G)]
+    r0 = np.full(G, 0.25, np.float32)
+    L, stored = upload_pool(S, luts, r0=r0, dtype=dtype, layout=layout)
+    Q = int(np.sum(counts))
+    dirs = I.directions(Q, seed + 100)
+    seg = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    rng = np.random.default_rng(seed + 101)
+    g = (rng.normal(size=Q).astype(np.float32), rng.normal(size=(Q, 3)).astype(np.float32),
+         rng.normal(size=(Q, 3)).astype(np.float32))
+    return luts, L, stored, r0, dirs, seg, g
+
+
+
+@pytest.mark.parametrize("N,dtype,layout", [(32, 0, 0), (12, 2, 0), (64, 0, 0), (20, 0, 1)])
+def test_deterministic_backward(S, N, dtype, layout):
+    """SHM_BWD_DETERMINISTIC: bit-identical dlut over repeated runs, the oracle's adjoint within the
+    atomic pass's tolerance, the same d/ddirs as the atomic pass.  N = 32 f32 and N = 12 bf16 texel
+    tables take the staged kernel, N = 64 (418 KB) and the cell layout read the footprint from
+    global memory; segments are ragged (0, 1, 1023, 1024, 1025 and 2500 queries)."""
+    counts = np.array([1025, 0, 2500, 1, 1024, 1023])
+    luts, L, stored, r0, dirs, seg, (gR, gG, gn) = _det_case(S, N, len(counts), counts, dtype, layout, 300 + N)
+    t = lambda a: torch.from_numpy(a).cuda()
+    outs = []
+    for _ in range(2):
+        dl = S.like_lut(L, dtype=0, layout=0, zero=True)
+        dd = S.query_backward(L, t(dirs), dl, gR=t(gR), ggrad=t(gG), gnormal=t(gn), seg=t(seg), deterministic=True)
+        outs.append((dl.data.clone(), dd))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    dla = S.like_lut(L, dtype=0, layout=0, zero=True)
+    dda = S.query_backward(L, t(dirs), dla, gR=t(gR), ggrad=t(gG), gnormal=t(gn), seg=t(seg))
+    assert torch.allclose(outs[0][1], dda, rtol=0, atol=1e-6 * float(dda.abs().max()))
+    off, Ns = O.make_pool(luts)[1:]
+    glyph = np.repeat(np.arange(len(counts)), counts).astype(np.int32)
+    dref, _ = O.query_vjp(stored.reshape(-1, 4), off, Ns, dirs, gR=gR, gG=gG, gn=gn, glyph=glyph,
+                          r0=r0.astype(np.float64), want_ddirs=False)
+    got = outs[0][0].view(-1, 4).double().cpu().numpy()
+    for ch in range(4):
+        scale = np.abs(dref[:, ch]).max()
+        assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * scale, ch
+
+
+def test_deterministic_backward_one_cell(S):
+    """Every query of a glyph in the same cell (one long run after the sort): the run's sum in
+    query order equals the oracle's."""
+    N = 16
+    luts, L, stored, r0, _, _, _ = _det_case(S, N, 2, [1, 1], 0, 0, 77)
+    Q = 3000
+    dirs = np.tile(np.array([[0.31, -0.22, 0.93]], np.float32), (Q, 1))
+    seg = np.array([0, Q, Q], np.int64)
+    rng = np.random.default_rng(78)
+    gR = rng.normal(size=Q).astype(np.float32)
+    t = lambda a: torch.from_numpy(a).cuda()
+    dl = S.like_lut(L, dtype=0, layout=0, zero=True)
+    S.query_backward(L, t(dirs), dl, gR=t(gR), seg=t(seg), deterministic=True, want_ddirs=False)
+    off, Ns = O.make_pool(luts)[1:]
+    dref, _ = O.query_vjp(stored.reshape(-1, 4), off, Ns, dirs, gR=gR, glyph=np.zeros(Q, np.int32),
+                          r0=r0.astype(np.float64), want_ddirs=False)
+    got = dl.data.view(-1, 4).double().cpu().numpy()
+    assert np.abs(got - dref).max() <= 2e-5 * np.abs(dref).max()
+
+
+def test_deterministic_needs_segments(S):
+    L, _ = upload_pool(S, [O.bake_sh(8, 2, I.sh_coeffs(1, 2, 5)[0])])
+    d = torch.from_numpy(I.directions(100, 6)).cuda()
+    dl = S.like_lut(L, dtype=0, layout=0, zero=True)
+    with pytest.raises(S.ShmError):
+        S.query_backward(L, d, dl, gR=torch.ones(100, device="cuda"), glyph=torch.zeros(100, dtype=torch.int32,
+                                                                                        device="cuda"),
+                         deterministic=True)
+    bad = S.alloc_lut(1, 9)  # resolution differs from the table's
+    with pytest.raises(S.ShmError):
+        S.query_backward(L, d, bad, gR=torch.ones(100, device="cuda"))
