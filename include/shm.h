@@ -267,9 +267,12 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
                               float* ddirs, uint32_t flags, int32_t* dev_status, shm_stream stream);
 
 /* Reverse mode of the SH bake: dcoeffs[g][k] (=) sum over texels and channels of
- * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L). */
+ * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L).
+ * flags = 0: the sum over texels is split across CTAs and combined with atomics when there are
+ * few (glyph, k) tiles; SHM_BWD_DETERMINISTIC: one thread sums each dcoeffs entry in a fixed order
+ * (bit-identical from run to run; slower for a handful of glyphs). */
 shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis,
-                                  float* dcoeffs, shm_stream stream);
+                                  float* dcoeffs, uint32_t flags, shm_stream stream);
 
 /* Fused fit loss and adjoint (not in the paper; fits tables to targets).  Per query the forward
  * of shm_query is recomputed and L_q = w_value (R - R_target)^2 + w_normal |n - n_target|^2 is

@@ -80,7 +80,7 @@ _SIGS = {
     "shm_lut_bounds": (C.c_int, [_VP, _VP, _VP]),
     "shm_build_mip": (C.c_int, [_VP, _VP, _VP, _VP]),
     "shm_query_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP, _VP]),
-    "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "shm_build_lut_backward": (C.c_int, [_VP, _I32, _VP, _VP, C.c_uint32, _VP]),
     "shm_fit_backward": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
     "shm_adam_step": (C.c_int, [_VP, _VP, _VP, _VP, _I64, C.c_float, C.c_float, C.c_float, C.c_float, _I32, _I32, _VP]),
     "shm_sh_eval": (C.c_int, [_I32, _I32, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -427,10 +427,11 @@ def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None,
     return ddirs
 
 
-def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None) -> torch.Tensor:
+def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None, deterministic=False) -> torch.Tensor:
     K = (L + 1) ** 2
     dc = torch.empty((dlut.n_glyphs, K), dtype=torch.float32, device=dlut.data.device)
-    _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc), _stream(stream)),
+    _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc),
+                                        C.c_uint32(SHM_BWD_DETERMINISTIC if deterministic else 0), _stream(stream)),
            "shm_build_lut_backward")
     return dc
 

@@ -489,15 +489,16 @@ shm_status shm_adam_step(float* param, float* grad, float* m, float* v, int64_t 
 }
 
 shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis, float* dcoeffs,
-                                  shm_stream stream)
+                                  uint32_t flags, shm_stream stream)
 {
     shm_status st = check_lut(dlut);
     if (st != SHM_OK) return st;
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL || dlut->N_uniform <= 0)
         return SHM_ERR_UNSUPPORTED;
     if (L < 0 || L > 20 || !basis || !dcoeffs) return SHM_ERR_INVALID_ARG;
+    if ((flags & ~(uint32_t)SHM_BWD_DETERMINISTIC) != 0) return SHM_ERR_INVALID_ARG;
     return map_cuda(launch_sh_build_bwd(dlut->N_uniform, dlut->n_glyphs, L, (const float*)dlut->data, basis, dcoeffs,
-                                        (cudaStream_t)stream));
+                                        (flags & SHM_BWD_DETERMINISTIC) != 0, (cudaStream_t)stream));
 }
 
 shm_status shm_sh_eval(int32_t L, int32_t n_glyphs, const float* coeffs, int64_t Q, const float* dirs,

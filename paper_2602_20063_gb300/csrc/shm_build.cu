@@ -261,7 +261,8 @@ cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* 
 }
 
 // dc[g][k] = sum_r dlut[g][r] basis[k][r], r over 4T scalars.  Tile 64 glyphs x 32 k, the
-// reduction split over blockIdx.z and combined with atomics into a zeroed dcoeffs.
+// reduction split over blockIdx.z and combined with atomics into a zeroed dcoeffs (one split, so
+// a fixed summation order, when the result must be deterministic).
 constexpr int BG = 64, BK = 32, BR = 32;
 
 __global__ void __launch_bounds__(256) k_sh_gemm_bwd(int R4, int G, int K, const float* __restrict__ dlut,
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(256) k_sh_gemm_bwd(int R4, int G, int K, const
         }
 }
 
-cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
+cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs, bool det,
                                 cudaStream_t s)
 {
     const int K = (L + 1) * (L + 1);
@@ -314,7 +315,7 @@ cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const fl
     cudaError_t e = cudaMemsetAsync(dcoeffs, 0, sizeof(float) * (size_t)G * K, s);
     if (e != cudaSuccess) return e;
     const int gx = (G + BG - 1) / BG, ky = (K + BK - 1) / BK;
-    int splits = (sm_count() * 4 + gx * ky - 1) / (gx * ky);
+    int splits = det ? 1 : (sm_count() * 4 + gx * ky - 1) / (gx * ky);
     const int max_splits = (R4 + BR - 1) / BR;
     if (splits > max_splits) splits = max_splits;
     if (splits < 1) splits = 1;

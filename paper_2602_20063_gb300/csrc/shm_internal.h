@@ -154,7 +154,7 @@ int sh_kpad(int L);
 int64_t sh_build_workspace_bytes(int G, int L);
 cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* coeffs, const float* basis,
                             cudaStream_t s);
-cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
+cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs, bool det,
                                 cudaStream_t s);
 cudaError_t launch_sh_value(const LutView& out, void* data, int L, const float* coeffs, cudaStream_t s);
 cudaError_t launch_query_recon(const QueryArgs& a, int method, cudaStream_t s);

@@ -141,3 +141,27 @@ def test_adam_vector_and_scalar_paths_agree(S):
     S.adam_step(B[0], B[1], B[2], B[3], lr=1e-2, step=3, zero_grad=True)
     for a, b in zip(A, B):
         assert torch.equal(a, b)
+
+
+def test_deterministic_gradients_through_the_bake(S):
+    """query_fn(..., deterministic=True): coefficient gradients bit-identical over two backward
+    passes, and equal to the atomic pass within float32 summation-order error; without segments the
+    deterministic pass is refused."""
+    N, L, G, per = 16, 6, 5, 3000
+    basis = S.sh_basis(N, L)
+    dirs = torch.from_numpy(I.directions(G * per, 90)).cuda()
+    seg = torch.from_numpy(I.query_glyphs_csr(G, per)).cuda()
+    grads = []
+    for det in (True, True, False):
+        c = torch.from_numpy(I.sh_coeffs(G, L, 89).astype(np.float32)).cuda().requires_grad_(True)
+        lut = S.alloc_lut(G, N)
+        table = S.sh_bake_fn(c, basis, lut, L, deterministic=det)
+        R, Gd, Nn = S.query_fn(table, dirs, lut, seg=seg, deterministic=det)
+        (R.sum() + 0.5 * Gd.square().sum() + Nn[:, 2].sum()).backward()
+        grads.append(c.grad.clone())
+    assert torch.equal(grads[0], grads[1])
+    assert float((grads[0] - grads[2]).abs().max()) <= 1e-5 * float(grads[2].abs().max())
+    lut = S.alloc_lut(G, N)
+    table = S.sh_bake_fn(torch.zeros((G, (L + 1) ** 2), device="cuda", requires_grad=True), basis, lut, L)
+    with pytest.raises(RuntimeError):
+        S.query_fn(table, dirs, lut, glyph=torch.zeros(G * per, dtype=torch.int32, device="cuda"), deterministic=True)
