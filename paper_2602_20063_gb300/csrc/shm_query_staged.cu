@@ -141,9 +141,9 @@ template <int DT>
 cudaError_t launch_staged_shape(const QueryArgs& a, uint32_t table_bytes, int shape, cudaStream_t s)
 {
     switch (shape) {
-    case 1: return launch_staged_t<DT, 1024>(a, table_bytes, s);
-    case 2: return launch_staged_t<DT, 256>(a, table_bytes, s);
-    default: return launch_staged_t<DT, 512>(a, table_bytes, s);
+    case 1: return launch_staged_t<DT, SSHAPES[1]>(a, table_bytes, s);
+    case 2: return launch_staged_t<DT, SSHAPES[2]>(a, table_bytes, s);
+    default: return launch_staged_t<DT, SSHAPES[0]>(a, table_bytes, s);
     }
 }
 
