@@ -2,9 +2,11 @@
 // (arXiv 2602.20063, §3.1; shading normals §3.4).
 //
 // The paper renders billboards through a raster pipeline; here there is no raster stage:
-//   k_rank_objects  orders objects front to back by |c - eye| - R_max (rank by counting);
-//   k_bin_tiles     one thread per 16x16 pixel tile walks the ordered objects and keeps those
-//                   whose conservative screen rectangle (from the bounding sphere) covers it;
+//   k_rank_objects  orders objects front to back by |c - eye| - R_max (rank by counting, keys
+//                   staged in shared memory 256 at a time);
+//   k_bin_tiles     one warp per 16x16 pixel tile walks the ordered objects 32 at a time and keeps,
+//                   in order (ballot compaction), those whose conservative screen rectangle (from
+//                   the bounding sphere) covers it;
 //   k_raycast       persistent CTAs take tiles from an atomic counter (no waits); per pixel and
 //                   candidate object: bounding-sphere chord [t_min, t_max] -> `march` samples of
 //                   F(x) = |x - c| - R(w) -> first sign change -> `bisect` halvings -> `newton`
@@ -47,20 +49,33 @@ __device__ __forceinline__ float depth_key(const shm_object& o, const shm_camera
     return sqrtf(dx * dx + dy * dy + dz * dz) - o.rmax;
 }
 
-__global__ void k_rank_objects(const shm_object* __restrict__ objs, int n, shm_camera cam, int32_t* order)
+constexpr int RANK_BLOCK = 256;
+
+// NaN keys sort last (treated as +inf, ties by index), so ranks stay a permutation of 0..n-1.
+__device__ __forceinline__ float rank_key(const shm_object& o, const shm_camera& cam)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    // NaN keys sort last (treated as +inf, ties by index), so ranks stay a permutation of 0..n-1
-    float ki = depth_key(objs[i], cam);
-    if (!(ki == ki)) ki = __int_as_float(0x7f800000);
+    const float k = depth_key(o, cam);
+    return (k == k) ? k : __int_as_float(0x7f800000);
+}
+
+__global__ void __launch_bounds__(RANK_BLOCK) k_rank_objects(const shm_object* __restrict__ objs, int n, shm_camera cam,
+                                                             int32_t* order)
+{
+    __shared__ float kt[RANK_BLOCK];
+    const int i = blockIdx.x * RANK_BLOCK + threadIdx.x;
+    const float ki = i < n ? rank_key(objs[i], cam) : 0.0f;
     int rank = 0;
-    for (int j = 0; j < n; ++j) {
-        float kj = depth_key(objs[j], cam);
-        if (!(kj == kj)) kj = __int_as_float(0x7f800000);
-        rank += (kj < ki) || (kj == ki && j < i);
+    for (int j0 = 0; j0 < n; j0 += RANK_BLOCK) {
+        __syncthreads();
+        if (j0 + (int)threadIdx.x < n) kt[threadIdx.x] = rank_key(objs[j0 + threadIdx.x], cam);
+        __syncthreads();
+        const int m = min(RANK_BLOCK, n - j0);
+        for (int jj = 0; jj < m; ++jj) {
+            const float kj = kt[jj];
+            rank += (kj < ki) || (kj == ki && j0 + jj < i);
+        }
     }
-    order[rank] = i;
+    if (i < n) order[rank] = i;
 }
 
 // Conservative pixel rectangle of a sphere (centre c, radius r): for every point p of the
@@ -94,26 +109,33 @@ __device__ __forceinline__ bool sphere_rect(const shm_object& o, const shm_camer
     return x0 <= x1 && y0 <= y1;
 }
 
-__global__ void k_bin_tiles(const shm_object* __restrict__ objs, int n, shm_camera cam, const int32_t* __restrict__ order,
-                            int32_t* counts, int32_t* lists)
+__global__ void __launch_bounds__(256) k_bin_tiles(const shm_object* __restrict__ objs, int n, shm_camera cam,
+                                                    const int32_t* __restrict__ order, int32_t* counts, int32_t* lists)
 {
     const int tx_n = (cam.W + RT - 1) / RT, ty_n = (cam.H + RT - 1) / RT;
-    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tile >= tx_n * ty_n) return;
+    const int tile = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (tile >= tx_n * ty_n) return;  // warp-uniform
     const int tx = tile % tx_n, ty = tile / tx_n;
     const int px0 = tx * RT, px1 = min(cam.W - 1, px0 + RT - 1), py0 = ty * RT, py1 = min(cam.H - 1, py0 + RT - 1);
     int cnt = 0;
     int32_t* out = lists + (int64_t)tile * n;
-    for (int q = 0; q < n; ++q) {
-        const int id = __ldg(order + q);
-        if (id < 0 || id >= n) continue;
-        const shm_object o = objs[id];
-        int x0, x1, y0, y1;
-        if (!sphere_rect(o, cam, x0, x1, y0, y1)) continue;
-        if (x1 < px0 || x0 > px1 || y1 < py0 || y0 > py1) continue;
-        out[cnt++] = id;
+    for (int q0 = 0; q0 < n; q0 += 32) {
+        const int q = q0 + lane;
+        int id = -1;
+        bool hit = false;
+        if (q < n) {
+            id = __ldg(order + q);
+            if (id >= 0 && id < n) {
+                const shm_object o = objs[id];
+                int x0, x1, y0, y1;
+                hit = sphere_rect(o, cam, x0, x1, y0, y1) && !(x1 < px0 || x0 > px1 || y1 < py0 || y0 > py1);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) out[cnt + __popc(m & ((1u << lane) - 1u))] = id;
+        cnt += __popc(m);
     }
-    counts[tile] = cnt;
+    if (lane == 0) counts[tile] = cnt;
 }
 
 struct Surf {
@@ -315,8 +337,8 @@ cudaError_t launch_raycast(const LutView& L, const shm_object* objs, int n_obj, 
     if (n_obj > 0) {
         e = cudaMemsetAsync(order, 0xff, 4LL * n_obj, s);
         if (e != cudaSuccess) return e;
-        k_rank_objects<<<(n_obj + 127) / 128, 128, 0, s>>>(objs, n_obj, cam, order);
-        k_bin_tiles<<<(tiles + 127) / 128, 128, 0, s>>>(objs, n_obj, cam, order, counts, lists);
+        k_rank_objects<<<(n_obj + RANK_BLOCK - 1) / RANK_BLOCK, RANK_BLOCK, 0, s>>>(objs, n_obj, cam, order);
+        k_bin_tiles<<<(unsigned)(((int64_t)tiles * 32 + 255) / 256), 256, 0, s>>>(objs, n_obj, cam, order, counts, lists);
     } else {
         e = cudaMemsetAsync(counts, 0, 4LL * tiles, s);
         if (e != cudaSuccess) return e;
