@@ -388,7 +388,9 @@ constexpr int FS = 18, MAX_BUMPS_SMEM = 128;
 
 // Gaussian bumps of one glyph, staged in shared memory: centre and amplitude as one float4 (a
 // broadcast 16-byte read), and the exponent factor with log2(e) folded in, so that
-//   a exp(-|w - mu|^2 / (2 width^2)) = a exp2(|w - mu|^2 k),  k = -log2(e) / (2 width^2).
+//   a exp(-|w - mu|^2 / (2 width^2)) = a exp2(|w - mu|^2 k),  k = -log2(e) / (2 width^2),
+// with 2^x from the PTX ex2.approx.ftz instruction (relative error about 2^-22; results below the
+// float32 normal range flush to zero, far below the sum's rounding error).
 struct BumpSmem {
     float4 m[MAX_BUMPS_SMEM];
     float k[MAX_BUMPS_SMEM];
@@ -404,13 +406,20 @@ __device__ __forceinline__ void stage_bumps(BumpSmem& B, const shm_source& src, 
     }
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float bump_sum(const BumpSmem& B, int nb, const Vec3& w, float sum)
 {
 #pragma unroll 4
     for (int q = 0; q < nb; ++q) {
         const float4 m = B.m[q];
         const float dx = w.x - m.x, dy = w.y - m.y, dz = w.z - m.z;
-        sum = fmaf(m.w, exp2f((dx * dx + dy * dy + dz * dz) * B.k[q]), sum);
+        sum = fmaf(m.w, ex2_approx((dx * dx + dy * dy + dz * dz) * B.k[q]), sum);
     }
     return sum;
 }
