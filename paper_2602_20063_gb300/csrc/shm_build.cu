@@ -687,7 +687,23 @@ cudaError_t launch_pack(const LutView& src, const LutView& dst, void* dst_data, 
 // cell's four corners (value weights are >= 0 and sum to 1; sum_a |H^d_a| = s(1-s) <= 1/4).
 constexpr int BOUNDS_PER_BLOCK = 2048;
 
-template <class Map>
+template <int DT, int LAYOUT>
+__device__ __forceinline__ float cell_bound(const LutView& L, const GlyphRef& G, int f, int i, int j)
+{
+    const Corners cr = fetch_corners<DT, LAYOUT>(L.data, G, f, i, j);
+    const float4 v[4] = {cr.c00, cr.c10, cr.c01, cr.c11};
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        m0 = fmaxf(m0, fabsf(G.r0 + v[k].x));
+        m1 = fmaxf(m1, fabsf(v[k].y));
+        m2 = fmaxf(m2, fabsf(v[k].z));
+        m3 = fmaxf(m3, fabsf(v[k].w));
+    }
+    return m0 + 0.25f * (m1 + m2) + 0.0625f * m3;
+}
+
+template <int DT, int LAYOUT, class Map>
 __global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, const __grid_constant__ Map map)
 {
     __shared__ float warp_best[8];
@@ -698,17 +714,17 @@ __global__ void __launch_bounds__(256) k_bounds(LutView L, float* rmax, const __
     const int64_t ncell = 6LL * P * P;
     const int64_t c_end = min(ncell, (int64_t)(blk + 1) * BOUNDS_PER_BLOCK);
     float best = 0.0f;
-    for (int64_t c = (int64_t)blk * BOUNDS_PER_BLOCK + threadIdx.x; c < c_end; c += blockDim.x) {
-        const int f = (int)(c / ((int64_t)P * P)), rem = (int)(c % ((int64_t)P * P)), j = rem / P, i = rem % P;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-        for (int corner = 0; corner < 4; ++corner) {
-            const float4 v = load_texel(L.data, L.dtype, L.layout, G, f, j + (corner >> 1), i + (corner & 1));
-            m0 = fmaxf(m0, fabsf(G.r0 + v.x));
-            m1 = fmaxf(m1, fabsf(v.y));
-            m2 = fmaxf(m2, fabsf(v.z));
-            m3 = fmaxf(m3, fabsf(v.w));
+    if (ncell <= 0x7fffffff) {  // 32-bit cell arithmetic (N < 18,900)
+        const uint32_t PP = (uint32_t)P * (uint32_t)P;
+        for (uint32_t c = (uint32_t)blk * BOUNDS_PER_BLOCK + threadIdx.x; c < (uint32_t)c_end; c += blockDim.x) {
+            const uint32_t f = c / PP, rem = c - f * PP, j = rem / (uint32_t)P, i = rem - j * (uint32_t)P;
+            best = fmaxf(best, cell_bound<DT, LAYOUT>(L, G, (int)f, (int)i, (int)j));
         }
-        best = fmaxf(best, m0 + 0.25f * (m1 + m2) + 0.0625f * m3);
+    } else {
+        for (int64_t c = (int64_t)blk * BOUNDS_PER_BLOCK + threadIdx.x; c < c_end; c += blockDim.x) {
+            const int f = (int)(c / ((int64_t)P * P)), rem = (int)(c % ((int64_t)P * P)), j = rem / P, i = rem % P;
+            best = fmaxf(best, cell_bound<DT, LAYOUT>(L, G, f, i, j));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
     if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
@@ -726,7 +742,17 @@ cudaError_t launch_bounds(const LutView& L, float* rmax, const Sizes& sz, cudaSt
     if (e != cudaSuccess) return e;
     auto blocks = [](int N) { return (6LL * (N + 1) * (N + 1) + BOUNDS_PER_BLOCK - 1) / BOUNDS_PER_BLOCK; };
     return for_each_glyph_chunk(sz, blocks, [&](unsigned bx, unsigned bz, const auto& map) {
-        k_bounds<<<dim3(bx, 1, bz), 256, 0, s>>>(L, rmax, map);
+        using M = std::decay_t<decltype(map)>;
+        const dim3 grid(bx, 1, bz);
+        if (L.layout == SHM_LAYOUT_TEXEL) {
+            if (L.dtype == SHM_F32) k_bounds<SHM_F32, SHM_LAYOUT_TEXEL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+            else if (L.dtype == SHM_F16) k_bounds<SHM_F16, SHM_LAYOUT_TEXEL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+            else k_bounds<SHM_BF16, SHM_LAYOUT_TEXEL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+        } else {
+            if (L.dtype == SHM_F32) k_bounds<SHM_F32, SHM_LAYOUT_CELL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+            else if (L.dtype == SHM_F16) k_bounds<SHM_F16, SHM_LAYOUT_CELL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+            else k_bounds<SHM_BF16, SHM_LAYOUT_CELL, M><<<grid, 256, 0, s>>>(L, rmax, map);
+        }
     });
 }
 
