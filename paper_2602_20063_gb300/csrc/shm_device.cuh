@@ -247,6 +247,20 @@ __device__ __forceinline__ HermOut hermite2(const Corners& c, float s, float t)
     return o;
 }
 
+// The value alone (same operations as hermite2's r), for callers that need no derivative.
+__device__ __forceinline__ float hermite_value(const Corners& c, float s, float t)
+{
+    const Herm a = herm(s), b = herm(t);
+    const float d0 = c.c10.x - c.c00.x, d1 = c.c11.x - c.c01.x;
+    const float e0 = c.c10.z - c.c00.z, e1 = c.c11.z - c.c01.z;
+    const float p0 = c.c00.x + a.H1 * d0 + a.h0d * c.c00.y + a.h1d * c.c10.y;
+    const float p1 = c.c01.x + a.H1 * d1 + a.h0d * c.c01.y + a.h1d * c.c11.y;
+    const float q0 = c.c00.z + a.H1 * e0 + a.h0d * c.c00.w + a.h1d * c.c10.w;
+    const float q1 = c.c01.z + a.H1 * e1 + a.h0d * c.c01.w + a.h1d * c.c11.w;
+    const float dp = p1 - p0;
+    return p0 + b.H1 * dp + b.h0d * q0 + b.h1d * q1;
+}
+
 // ------------------------------------------------------------------------------------------
 // §3.4: the Cramer solution of G [alpha beta]^T = [R_u R_v]^T in closed form.  With
 // w~ = a + x b + y c, rho = |w~|, e1 = (2/rho)(I - w w^T) b, e2 = (2/rho)(I - w w^T) c, the

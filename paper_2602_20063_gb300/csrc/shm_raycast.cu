@@ -164,6 +164,24 @@ __device__ __forceinline__ bool surface_F(const LutView& L, const GlyphRef& G, f
     return true;
 }
 
+// F alone at t (march and bisection need only its sign): chart, cell, footprint and the Hermite
+// value, no derivatives.  Same value as surface_F's S.F.
+template <int DT, int LAYOUT>
+__device__ __forceinline__ bool surface_value(const LutView& L, const GlyphRef& G, float scale, const float* c,
+                                              const float* o, const Vec3& d, float t, float& F)
+{
+    const float x0 = o[0] + t * d.x - c[0], x1 = o[1] + t * d.y - c[1], x2 = o[2] + t * d.z - c[2];
+    Chart ch;
+    if (!chart_of(x0, x1, x2, ch)) return false;
+    int i, j;
+    float s, tt;
+    cell_of(pick3(ch.k1, x0, x1, x2), ch.m, ch.im, G.N, i, s);
+    cell_of(pick3(ch.k2, x0, x1, x2), ch.m, ch.im, G.N, j, tt);
+    const float R = G.r0 + hermite_value(fetch_corners<DT, LAYOUT>(L.data, G, ch.f, i, j), s, tt);
+    F = sqrtf(x0 * x0 + x1 * x1 + x2 * x2) - scale * fabsf(R);
+    return true;
+}
+
 // Refinement steps of one object by its projected radius (see shm_raycast_params).  The radius
 // decides integers, so it is formed with round-to-nearest intrinsics (no contraction into FMA),
 // operation by operation as written.
@@ -248,18 +266,19 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
             const GlyphRef G = glyph_ref(L, ob.glyph);
             Surf S;
             float thit = qnan;
-            if (!surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t0, S)) { status |= SHM_DEV_NONFINITE; continue; }
+            float F;
+            if (!surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t0, F)) { status |= SHM_DEV_NONFINITE; continue; }
             ++nq;
-            if (S.F < 0.0f) {
+            if (F < 0.0f) {
                 thit = t0;
             } else {
                 float lo = t0, hi = t0;
                 bool found = false;
                 for (int k = 1; k <= prm.march; ++k) {
                     const float tk = t0 + (t1 - t0) * (float)k / (float)prm.march;
-                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, tk, S);
+                    surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, tk, F);
                     ++nq;
-                    if (S.F < 0.0f) {
+                    if (F < 0.0f) {
                         lo = t0 + (t1 - t0) * (float)(k - 1) / (float)prm.march;
                         hi = tk;
                         found = true;
@@ -269,9 +288,9 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
                 if (!found) continue;
                 for (int it = 0; it < n_bisect; ++it) {
                     const float mid = 0.5f * (lo + hi);
-                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, mid, S);
+                    surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, mid, F);
                     ++nq;
-                    if (S.F < 0.0f) hi = mid; else lo = mid;
+                    if (F < 0.0f) hi = mid; else lo = mid;
                 }
                 float t = 0.5f * (lo + hi);
                 for (int it = 0; it < n_newton; ++it) {
