@@ -7,7 +7,8 @@
 //   k_bin_tiles     one warp per 16x16 pixel tile walks the ordered objects 32 at a time and keeps,
 //                   in order (ballot compaction), those whose conservative screen rectangle (from
 //                   the bounding sphere) covers it;
-//   k_raycast       persistent CTAs take tiles from an atomic counter (no waits); per pixel and
+//   k_raycast       persistent warps take 16x2-pixel strips of a tile from an atomic counter (no
+//                   waits, no CTA barriers: a warp moves on as soon as its own pixels are done); per pixel and
 //                   candidate object: bounding-sphere chord [t_min, t_max] -> `march` samples of
 //                   F(x) = |x - c| - R(w) -> first sign change -> `bisect` halvings -> `newton`
 //                   Newton steps with F' = d.(w - grad_{S^2}R/|x - c|) -> nearest hit -> normal
@@ -213,9 +214,9 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
                                                     unsigned long long* query_counter, float* rgba, float* depth,
                                                     float* normal, int32_t* obj_id, int32_t* dev_status)
 {
-    __shared__ int s_tile;
     const int tx_n = (cam.W + RT - 1) / RT, ty_n = (cam.H + RT - 1) / RT;
-    const int ntiles = tx_n * ty_n;
+    const int nunits = tx_n * ty_n * (RT / 2);  // a unit = two pixel rows of a tile = one warp
+    const int lane = threadIdx.x & 31;
     const float qnan = __int_as_float(0x7fc00000);
     uint32_t status = 0;
     unsigned long long nq = 0;
@@ -226,12 +227,12 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
     }
     const float aspect = (float)cam.W / (float)cam.H;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
-        __syncthreads();
-        const int tile = s_tile;
-        __syncthreads();
-        if (tile >= ntiles) break;
-        const int px = (tile % tx_n) * RT + (threadIdx.x % RT), py = (tile / tx_n) * RT + (threadIdx.x / RT);
+        int unit = 0;
+        if (lane == 0) unit = (int)atomicAdd(tile_counter, 1u);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= nunits) break;  // warp-uniform
+        const int tile = unit / (RT / 2), strip = unit % (RT / 2);
+        const int px = (tile % tx_n) * RT + (lane % RT), py = (tile / tx_n) * RT + 2 * strip + lane / RT;
         if (px >= cam.W || py >= cam.H) continue;
         const float xn = (2.0f * (px + 0.5f) / cam.W - 1.0f) * cam.tan_half_fov_y * aspect;
         const float yn = (1.0f - 2.0f * (py + 0.5f) / cam.H) * cam.tan_half_fov_y;
