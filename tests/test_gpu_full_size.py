@@ -17,7 +17,7 @@ import torch
 import oracle as O
 import oracle.fit as OF
 import shm_inputs as I
-from gpu_common import check_query, shm
+from gpu_common import check_query, near_edge, shm
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +86,45 @@ def test_fit_full_size(S):
         for ch in range(4):
             assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * np.abs(dref[:, ch]).max(), (g, ch)
     assert torch.isfinite(loss).all() and loss.item() > 0
+
+
+def test_glyph_field_backward_full_size(S):
+    """Reverse pass of the glyph field at the bench size (16,384 tcgen05-baked tables, 2^26 queries
+    in segments), atomic and deterministic: the gradient slabs of sampled glyphs against the
+    oracle's adjoint of those glyphs' queries; the deterministic pass bit-identical over two runs.
+    d/ddirs goes through the patch's second derivatives and two chart scalings (d/ds = N d/du, and
+    s moves by N/2 per unit of the chart coordinate), so float32 rounding in the Hermite sums grows
+    by about N^2: it is compared within 8 N^2 2^-24 of its largest magnitude (4.9e-4 at N = 32)."""
+    G, L, N, per = 16384, 8, 32, 4096
+    Q = G * per
+    coeffs = I.sh_coeffs(G, L, 20063 + 1).astype(np.float32)
+    lut = S.alloc_lut(G, N)
+    src = S.Source(kind=S.SHM_SRC_SH, L=L, coeffs=torch.from_numpy(coeffs).cuda(), basis=S.sh_basis(N, L))
+    S.build_lut(lut, src, ws=S.build_workspace(lut, src))
+    dirs = np.empty((Q, 3), np.float32)
+    for s0, d in I.directions_chunked(Q, 20063 + 1 + 7):
+        dirs[s0:s0 + len(d)] = d
+    rng = np.random.default_rng(13)
+    up = rng.standard_normal((Q, 7), dtype=np.float32)
+    seg = torch.from_numpy(I.query_glyphs_csr(G, per)).cuda()
+    d = torch.from_numpy(dirs).cuda()
+    u = torch.from_numpy(up).cuda()
+    gR, gG, gN = u[:, 0].contiguous(), u[:, 1:4].contiguous(), u[:, 4:7].contiguous()
+    res = {}
+    for name, det in (("atomic", False), ("det1", True), ("det2", True)):
+        dl = S.like_lut(lut, dtype=0, layout=0, zero=True)
+        dd = S.query_backward(lut, d, dl, gR=gR, ggrad=gG, gnormal=gN, seg=seg, deterministic=det)
+        res[name] = (dl.data.view(G, -1, 4), dd)
+    assert torch.equal(res["det1"][0], res["det2"][0]) and torch.equal(res["det1"][1], res["det2"][1])
+    table = lut.data.view(G, -1, 4)
+    for g in (0, 7777, G - 1):
+        sl = slice(g * per, (g + 1) * per)
+        pool, off, Ns = O.make_pool([table[g].double().cpu().numpy().reshape(6, N + 2, N + 2, 4)])
+        dref, ddref = O.query_vjp(pool, off, Ns, dirs[sl], gR=up[sl, 0], gG=up[sl, 1:4], gn=up[sl, 4:7])
+        for name in ("atomic", "det1"):
+            got = res[name][0][g].double().cpu().numpy()
+            for ch in range(4):
+                assert np.abs(got[:, ch] - dref[:, ch]).max() <= 2e-5 * np.abs(dref[:, ch]).max(), (name, g, ch)
+            dd = res[name][1][sl].double().cpu().numpy()
+            ok = ~near_edge(None, dirs[sl], [N], None, eps=1e-4)
+            assert np.abs(dd[ok] - ddref[ok]).max() <= 8 * N * N * 2.0 ** -24 * np.abs(ddref[ok]).max(), (name, g)
