@@ -375,16 +375,42 @@ __device__ float fbm(const Vec3& w, const shm_source& src)
     float sum = 0.0f, freq = src.base_freq, amp = 1.0f;
     for (int o = 0; o < src.octaves; ++o) {
         const uint32_t* key = src.keys + 3 * o;
-        sum += amp * value_noise(w.x * freq, w.y * freq, w.z * freq, __ldg(key), __ldg(key + 1), __ldg(key + 2));
+        sum = fmaf(amp, value_noise(w.x * freq, w.y * freq, w.z * freq, __ldg(key), __ldg(key + 1), __ldg(key + 2)), sum);
         freq *= src.lacunarity;
         amp *= src.gain;
     }
     return src.amplitude * sum;
 }
 
+// value_noise with the lattice values read from a table of the box [x0, x0+nx) x [y0, ...) x
+// [z0, ...) (same corners and interpolation, so the same result).
+__device__ __forceinline__ float value_noise_box(float px, float py, float pz, const float* T, int x0, int y0, int z0,
+                                                 int nx, int ny, int nz)
+{
+    const float fx = floorf(px), fy = floorf(py), fz = floorf(pz);
+    const float wx = quintic(px - fx), wy = quintic(py - fy), wz = quintic(pz - fz);
+    // the corner stays inside the box (the callers' box is padded; the clamps only guard it)
+    const int nxy = nx * ny;
+    const int bx = min(max((int)fx - x0, 0), nx - 2), by = min(max((int)fy - y0, 0), ny - 2);
+    const int bz = min(max((int)fz - z0, 0), nz - 2);
+    const float* b = T + bz * nxy + by * nx + bx;
+    float c[2][2];
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy) {
+            const float* r = b + dz * nxy + dy * nx;
+            const float v0 = r[0], v1 = r[1];
+            c[dz][dy] = v0 + wx * (v1 - v0);
+        }
+    const float e0 = c[0][0] + wy * (c[0][1] - c[0][0]);
+    const float e1 = c[1][0] + wy * (c[1][1] - c[1][0]);
+    return e0 + wz * (e1 - e0);
+}
+
 // ------------------------------------------------------------------------------------------
 // Sampled sources: value tables (k_value_build) and finite-difference records (k_fd_face).
 constexpr int FS = 18, MAX_BUMPS_SMEM = 128;
+constexpr int FBM_CACHE = 4096;  // lattice values of the octaves' boxes per CTA (16 KB)
+constexpr int FBM_MAX_OCT = 16;  // octaves whose boxes may be cached
 
 // Gaussian bumps of one glyph, staged in shared memory: centre and amplitude as one float4 (a
 // broadcast 16-byte read), and the exponent factor with log2(e) folded in, so that
@@ -521,14 +547,108 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                     (a.z + X * bb.z + Y * cc.z) * ir};
     };
     const int S = N + 4;
-    for (int e = tid; e < Si * Sj; e += 256) {
-        const int ii = i0 + e % Si, jj = j0 + e / Si;
-        float v = 0.0f;
-        if (src.kind == SHM_SRC_SAMPLES)
-            v = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
-        else if (src.kind == SHM_SRC_FBM)
-            v = fbm(dir(ii, jj), src);
-        Sf[e] = v;
+    if (src.kind == SHM_SRC_FBM) {
+        // fBm over the region with the lattice values in shared memory: the corners an octave of
+        // frequency f needs lie in the box [floor(f wmin), floor(f wmax) + 1] per axis (floor(f w)
+        // is monotone in w), padded by one lattice step on each side; the boxes of all octaves that
+        // fit are hashed once, the others are hashed per sample.  Chart coordinates X, Y of the
+        // region's columns and rows are divided once.
+        __shared__ float cache[FBM_CACHE];
+        __shared__ float s_w[8][6];
+        __shared__ float s_xy[2 * (REGION_T + 2)];
+        __shared__ int s_box[FBM_MAX_OCT][8];  // x0, y0, z0, nx, ny, nz, cache offset, boxed
+        const bool xy_tab = (Si <= REGION_T + 2 && Sj <= REGION_T + 2);  // block-uniform
+        if (xy_tab) {
+            for (int e = tid; e < Si + Sj; e += 256) {
+                const int g2 = (e < Si) ? 2 * (i0 + e) : 2 * (j0 + e - Si);
+                s_xy[e] = (float)(g2 - 3 - N) / (float)N;
+            }
+            __syncthreads();
+        }
+        auto wdir = [&](int li, int lj) {
+            if (!xy_tab) return dir(i0 + li, j0 + lj);
+            const float X = s_xy[li], Y = s_xy[Si + lj];
+            const float ir = rsqrtf(1.0f + X * X + Y * Y);
+            return Vec3{(a.x + X * bb.x + Y * cc.x) * ir, (a.y + X * bb.y + Y * cc.y) * ir,
+                        (a.z + X * bb.z + Y * cc.z) * ir};
+        };
+        float lo[3] = {3.0f, 3.0f, 3.0f}, hi[3] = {-3.0f, -3.0f, -3.0f};
+        for (int e = tid; e < Si * Sj; e += 256) {
+            const Vec3 w = wdir(e % Si, e / Si);
+            lo[0] = fminf(lo[0], w.x); lo[1] = fminf(lo[1], w.y); lo[2] = fminf(lo[2], w.z);
+            hi[0] = fmaxf(hi[0], w.x); hi[1] = fmaxf(hi[1], w.y); hi[2] = fmaxf(hi[2], w.z);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int a3 = 0; a3 < 3; ++a3) {
+                lo[a3] = fminf(lo[a3], __shfl_xor_sync(0xffffffffu, lo[a3], o));
+                hi[a3] = fmaxf(hi[a3], __shfl_xor_sync(0xffffffffu, hi[a3], o));
+            }
+        if ((tid & 31) == 0)
+            for (int a3 = 0; a3 < 3; ++a3) { s_w[tid >> 5][a3] = lo[a3]; s_w[tid >> 5][3 + a3] = hi[a3]; }
+        __syncthreads();
+        const int octaves = min(src.octaves, FBM_MAX_OCT);
+        if (tid == 0) {
+            for (int a3 = 0; a3 < 3; ++a3) {
+                lo[a3] = s_w[0][a3];
+                hi[a3] = s_w[0][3 + a3];
+                for (int wp = 1; wp < 8; ++wp) { lo[a3] = fminf(lo[a3], s_w[wp][a3]); hi[a3] = fmaxf(hi[a3], s_w[wp][3 + a3]); }
+            }
+            float freq = src.base_freq;
+            int used = 0;
+            for (int o = 0; o < octaves; ++o) {
+                int* bx = s_box[o];
+                bx[0] = (int)floorf(lo[0] * freq) - 1;
+                bx[1] = (int)floorf(lo[1] * freq) - 1;
+                bx[2] = (int)floorf(lo[2] * freq) - 1;
+                bx[3] = (int)floorf(hi[0] * freq) - bx[0] + 3;
+                bx[4] = (int)floorf(hi[1] * freq) - bx[1] + 3;
+                bx[5] = (int)floorf(hi[2] * freq) - bx[2] + 3;
+                const int64_t n = (int64_t)bx[3] * bx[4] * bx[5];
+                bx[6] = used;
+                bx[7] = (used + n <= FBM_CACHE) ? 1 : 0;
+                if (bx[7]) used += (int)n;
+                freq *= src.lacunarity;
+            }
+        }
+        __syncthreads();
+        for (int o = 0; o < octaves; ++o) {
+            const int* bx = s_box[o];
+            if (!bx[7]) continue;  // block-uniform
+            const int nx = bx[3], ny = bx[4], n = nx * ny * bx[5];
+            const uint32_t k0 = __ldg(src.keys + 3 * o), k1 = __ldg(src.keys + 3 * o + 1), k2 = __ldg(src.keys + 3 * o + 2);
+            for (int idx = tid; idx < n; idx += 256) {
+                const int ix = idx % nx, iy = (idx / nx) % ny, iz = idx / (nx * ny);
+                cache[bx[6] + idx] = lattice_value(bx[0] + ix, bx[1] + iy, bx[2] + iz, k0, k1, k2);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < Si * Sj; e += 256) {
+            const Vec3 w = wdir(e % Si, e / Si);
+            float sum = 0.0f, freq = src.base_freq, amp = 1.0f;
+            for (int o = 0; o < src.octaves; ++o) {
+                const float px = w.x * freq, py = w.y * freq, pz = w.z * freq;
+                float v;
+                if (o < FBM_MAX_OCT && s_box[o][7]) {
+                    const int* bx = s_box[o];
+                    v = value_noise_box(px, py, pz, cache + bx[6], bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]);
+                } else {
+                    const uint32_t* key = src.keys + 3 * o;
+                    v = value_noise(px, py, pz, __ldg(key), __ldg(key + 1), __ldg(key + 2));
+                }
+                sum = fmaf(amp, v, sum);
+                freq *= src.lacunarity;
+                amp *= src.gain;
+            }
+            Sf[e] = src.amplitude * sum;
+        }
+    } else {
+        for (int e = tid; e < Si * Sj; e += 256) {
+            const int ii = i0 + e % Si, jj = j0 + e / Si;
+            float v = 0.0f;
+            if (src.kind == SHM_SRC_SAMPLES)
+                v = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
+            Sf[e] = v;
+        }
     }
     float base = 0.0f;
     if (src.kind == SHM_SRC_BUMPS) {
