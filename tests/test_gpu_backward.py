@@ -103,16 +103,17 @@ def test_build_backward(S, N, L, G):
         assert np.abs(dc[g] - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dtype", [0, 1])
-def test_segments_and_glyph_ids_agree_with_oracle(S, dtype):
+@pytest.mark.parametrize("dtype,N", [(0, 14), (1, 14), (0, 64), (1, 64)])
+def test_segments_and_glyph_ids_agree_with_oracle(S, dtype, N):
     """The reverse pass with CSR segments and with glyph ids on the same queries, both against the
     oracle, accumulating into a non-zero dL/dtable, with queries outside every segment (NaN
-    direction gradients, SHM_DEV_BOUNDS) and an empty segment."""
-    G, N = 7, 14
+    direction gradients, SHM_DEV_BOUNDS) and an empty segment.  N = 14 stages whole tables in the
+    segment pass; N = 64 (418 KB tables) reads the footprints from global memory in both."""
+    G = 7
     luts = [O.bake_sh(N, 5, I.sh_coeffs(1, 5, 600 + g)[0] + np.eye(1, 36, 0)[0] * 2.0) for g in range(G)]
     r0 = np.linspace(0.0, 0.4, G).astype(np.float32)
     L, stored = upload_pool(S, luts, r0=r0, dtype=dtype)
-    counts = np.array([700, 0, 4096, 33, 1500, 2, 999])
+    counts = np.array([700, 0, 4096, 33, 1500, 2, 9000 if N == 64 else 999])
     pre, post = 5, 9
     Q = pre + int(counts.sum()) + post
     dirs = I.directions(Q, 601)
