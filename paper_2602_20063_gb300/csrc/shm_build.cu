@@ -519,12 +519,13 @@ __global__ void __launch_bounds__(256) k_value_build(LutView out, void* data, sh
 constexpr int FACE_N_MAX = 144;  // (N+4)^2 floats <= 87.6 KB
 constexpr int REGION_T = 64;     // region edge for larger tables: 66^2 floats = 17.4 KB
 
-template <class Map>
+// FBM: the fBm source (its lattice cache is only allocated in that instantiation); otherwise stored
+// samples or Gaussian bumps.
+template <bool FBM, class Map>
 __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_source src, int T,
                                                  const __grid_constant__ Map map)
 {
     extern __shared__ float Sf[];  // [T+2][T+2]
-    __shared__ BumpSmem bump;
     int region;
     const int g = map_block(map, region), f = blockIdx.y;
     const GlyphRef Gr = glyph_ref(out, g);
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                     (a.z + X * bb.z + Y * cc.z) * ir};
     };
     const int S = N + 4;
-    if (src.kind == SHM_SRC_FBM) {
+    float base = 0.0f;
+    if constexpr (FBM) {
         // fBm over the region with the lattice values in shared memory: the corners an octave of
         // frequency f needs lie in the box [floor(f wmin), floor(f wmax) + 1] per axis (floor(f w)
         // is monotone in w), padded by one lattice step on each side; the boxes of all octaves that
@@ -642,6 +644,7 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
             Sf[e] = src.amplitude * sum;
         }
     } else {
+        __shared__ BumpSmem bump;
         for (int e = tid; e < Si * Sj; e += 256) {
             const int ii = i0 + e % Si, jj = j0 + e / Si;
             float v = 0.0f;
@@ -649,17 +652,16 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                 v = __ldg(src.samples + __ldg(src.sample_offset + g) + ((int64_t)f * S + jj) * S + ii) - Gr.r0;
             Sf[e] = v;
         }
-    }
-    float base = 0.0f;
-    if (src.kind == SHM_SRC_BUMPS) {
-        base = 1.0f - Gr.r0;
-        const int64_t b_lo = __ldg(src.bump_offset + g), b_hi = __ldg(src.bump_offset + g + 1);
-        for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
-            const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
-            __syncthreads();
-            stage_bumps(bump, src, bc, nb);
-            __syncthreads();
-            for (int e = tid; e < Si * Sj; e += 256) Sf[e] = bump_sum(bump, nb, dir(i0 + e % Si, j0 + e / Si), Sf[e]);
+        if (src.kind == SHM_SRC_BUMPS) {
+            base = 1.0f - Gr.r0;
+            const int64_t b_lo = __ldg(src.bump_offset + g), b_hi = __ldg(src.bump_offset + g + 1);
+            for (int64_t bc = b_lo; bc < b_hi; bc += MAX_BUMPS_SMEM) {
+                const int nb = (int)min((int64_t)MAX_BUMPS_SMEM, b_hi - bc);
+                __syncthreads();
+                stage_bumps(bump, src, bc, nb);
+                __syncthreads();
+                for (int e = tid; e < Si * Sj; e += 256) Sf[e] = bump_sum(bump, nb, dir(i0 + e % Si, j0 + e / Si), Sf[e]);
+            }
         }
     }
     __syncthreads();
@@ -690,22 +692,27 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
     {
         const int T = (sz.max_N <= FACE_N_MAX) ? sz.max_N + 2 : REGION_T;
         const int smem = (T + 2) * (T + 2) * (int)sizeof(float);
-        static int configured[2] = {0, 0};
-        const int mi = sz.N_uniform > 0 ? 0 : 1;
-        if (configured[mi] < smem) {
-            cudaError_t e = (mi == 0) ? cudaFuncSetAttribute(k_fd_face<UniformMap>,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                                      : cudaFuncSetAttribute(k_fd_face<TileMap>,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        static int configured[2][2] = {{0, 0}, {0, 0}};
+        const int mi = sz.N_uniform > 0 ? 0 : 1, fi = src.kind == SHM_SRC_FBM ? 1 : 0;
+        if (configured[fi][mi] < smem) {
+            auto attr = [smem](const void* fn) {
+                return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            };
+            cudaError_t e = fi ? (mi == 0 ? attr((const void*)k_fd_face<true, UniformMap>)
+                                          : attr((const void*)k_fd_face<true, TileMap>))
+                               : (mi == 0 ? attr((const void*)k_fd_face<false, UniformMap>)
+                                          : attr((const void*)k_fd_face<false, TileMap>));
             if (e != cudaSuccess) return e;
-            configured[mi] = smem;
+            configured[fi][mi] = smem;
         }
         auto regions = [T](int N) {
             const int64_t r = (N + 2 + T - 1) / T;
             return r * r;
         };
         return for_each_glyph_chunk(sz, regions, [&](unsigned bx, unsigned bz, const auto& map) {
-            k_fd_face<std::decay_t<decltype(map)>><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, T, map);
+            using M = std::decay_t<decltype(map)>;
+            if (fi) k_fd_face<true, M><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, T, map);
+            else k_fd_face<false, M><<<dim3(bx, 6, bz), 256, smem, s>>>(out, data, src, T, map);
         });
     }
 }
