@@ -29,7 +29,7 @@ constexpr int BCHUNK = 4;
 constexpr int BBLOCK = 256;
 
 template <int DT, int LAYOUT, bool FIT>
-__global__ void __launch_bounds__(BBLOCK, 3) k_query_bwd(BackwardArgs a)
+__global__ void __launch_bounds__(BBLOCK, 4) k_query_bwd(BackwardArgs a)
 {
     float loss_acc = 0.0f;
     const int lane = threadIdx.x & 31;
