@@ -1042,21 +1042,45 @@ class Fit:
         torch = self.torch
         self.hsets = [(d.cpu().pin_memory(), R.cpu().pin_memory(), n.cpu().pin_memory()) for d, R, n in self.sets]
         host_out = {"loss": torch.empty(1).pin_memory()}
+        self.copy_stream = torch.cuda.Stream()
+        self.copied = [None] * self.n_sets  # event: that set's host-to-device copy is done
         d, R, n = self.sets[0]
         return host_out, (d.numel() + R.numel() + n.numel()) * 4, 4
 
-    def e2e_step(self, host_out):
-        i = self.k % self.n_sets
+    def _copy_set(self, i, stream):
         d, Rt, nt = self.sets[i]
         hd, hR, hn = self.hsets[i]
-        d.copy_(hd, non_blocking=True)
-        Rt.copy_(hR, non_blocking=True)
-        nt.copy_(hn, non_blocking=True)
+        with self.torch.cuda.stream(stream):
+            d.copy_(hd, non_blocking=True)
+            Rt.copy_(hR, non_blocking=True)
+            nt.copy_(hn, non_blocking=True)
+            ev = self.torch.cuda.Event()
+            ev.record(stream)
+        self.copied[i] = ev
+
+    def e2e_step(self, host_out):
+        """One training step from page-locked host memory, as a data loader would run it: this
+        step's directions and targets arrived over the host link while the previous step computed
+        (a second stream; the first step copies its own), the fused forward + loss + adjoint and
+        Adam run while the next step's inputs copy, and the loss comes back."""
+        torch = self.torch
+        main = torch.cuda.current_stream()
+        i, j = self.k % self.n_sets, (self.k + 1) % self.n_sets
+        if self.copied[i] is None:
+            self._copy_set(i, main)
+        main.wait_event(self.copied[i])
+        self.copied[i] = None
+        # set j was last read three steps ago; the copy stream starts after this step's start
+        self.copy_stream.wait_stream(main)
+        self._copy_set(j, self.copy_stream)
+        d, Rt, nt = self.sets[i]
         self.loss.zero_()
         self.k += 1
         self.S.fit_backward(self.lut, d, Rt, nt, self.dl, 1.0, 1.0, loss=self.loss, seg=self.seg)
         self.S.adam_step(self.lut.data, self.dl.data, self.m, self.v, lr=1e-2, step=self.k)
         host_out["loss"].copy_(self.loss, non_blocking=True)
+        # the step ends when the next step's inputs have landed too: one copy per step is timed
+        main.wait_stream(self.copy_stream)
 
     def roofline_terms(self, peaks, ktot, sms):
         T = 6 * (self.N + 2) ** 2
