@@ -647,16 +647,34 @@ class Planet:
         host_out = {k: torch.empty(v.shape, dtype=torch.float32).pin_memory() for k, v in self.out.items()}
         h2d = (self.dr.numel() + self.dc.numel()) * 4
         d2h = 2 * sum(v.numel() * 4 for v in self.out.values())
+        self.e2e_streams = [torch.cuda.Stream() for _ in range(3)]
+        self.e2e_chunks = 8
         return host_out, h2d, d2h
 
     def e2e_step(self, host_out):
-        self.dr.copy_(self.hr, non_blocking=True)
-        self.dc.copy_(self.hc, non_blocking=True)
+        """Public API from page-locked host memory: the bake, then both query sets in chunks that
+        rotate over three streams (a chunk's directions copy in, its queries run and its outputs copy
+        out while its neighbours do the same), so the host link carries traffic both ways at once.
+        Chunk c of both sets shares a stream, so the device output buffer is reused in order."""
+        torch = self.torch
+        main = torch.cuda.current_stream()
         self.bake()
-        for d in (self.dr, self.dc):
-            self.S.query(self.lut, d, out=self.out)
-            for k in ("R", "grad", "normal"):
-                host_out[k].copy_(self.out[k], non_blocking=True)
+        for st in self.e2e_streams:
+            st.wait_stream(main)
+        n = self.Qr
+        step = (n + self.e2e_chunks - 1) // self.e2e_chunks
+        for d, h in ((self.dr, self.hr), (self.dc, self.hc)):
+            for c, q0 in enumerate(range(0, n, step)):
+                q1 = min(n, q0 + step)
+                st = self.e2e_streams[c % len(self.e2e_streams)]
+                with torch.cuda.stream(st):
+                    d[q0:q1].copy_(h[q0:q1], non_blocking=True)
+                    o = {k: v[q0:q1] for k, v in self.out.items()}
+                    self.S.query(self.lut, d[q0:q1], out=o, stream=st)
+                    for k in ("R", "grad", "normal"):
+                        host_out[k][q0:q1].copy_(o[k], non_blocking=True)
+        for st in self.e2e_streams:
+            main.wait_stream(st)
 
     def roofline_terms(self, peaks, ktot, sms):
         rec = self.S.record_bytes(self.dtype, self.layout) * (1 if self.layout == 1 else 4)
@@ -894,18 +912,42 @@ class Impostors:
         self.h_amp = self.src.amp.cpu().pin_memory()
         self.h_w = self.src.width.cpu().pin_memory()
         host_out = {"rgba": torch.empty((self.H, self.W, 4)).pin_memory()}
+        # two device colour buffers: a frame's image copies back while the next frame renders
+        self.rgba2 = [self.out["rgba"], torch.empty_like(self.out["rgba"])]
+        self.copy_stream = torch.cuda.Stream()
+        self.copy_done = [None, None]
+        self.frame = 0
         h2d = (self.h_mu.numel() + self.h_amp.numel() + self.h_w.numel()) * 4
         d2h = self.W * self.H * 16
         return host_out, h2d, d2h
 
     def e2e_step(self, host_out):
+        """One frame through the public API: the bump parameters come from page-locked host memory,
+        the objects are baked and bounded, the frame is ray cast into one of two colour buffers and
+        copied back on a second stream while the next frame renders.  A step ends when the previous
+        frame's image has landed, so one image copy is timed per step."""
+        torch = self.torch
+        main = torch.cuda.current_stream()
+        b = self.frame % 2
+        if self.copy_done[b] is not None:
+            main.wait_event(self.copy_done[b])  # this buffer's last image has been read back
         self.src.mu.copy_(self.h_mu, non_blocking=True)
         self.src.amp.copy_(self.h_amp, non_blocking=True)
         self.src.width.copy_(self.h_w, non_blocking=True)
         self.S.build_lut(self.lut, self.src)
-        self.objs.view(self.torch.float32).view(-1, 6)[:, 4].copy_(self.S.lut_bounds(self.lut))
-        self.S.raycast(self.lut, self.objs, self.n, self.cam, self.prm, ws=self.ws, out=self.out)
-        host_out["rgba"].copy_(self.out["rgba"], non_blocking=True)
+        self.objs.view(torch.float32).view(-1, 6)[:, 4].copy_(self.S.lut_bounds(self.lut))
+        out = dict(self.out, rgba=self.rgba2[b])
+        self.S.raycast(self.lut, self.objs, self.n, self.cam, self.prm, ws=self.ws, out=out)
+        self.copy_stream.wait_stream(main)
+        with torch.cuda.stream(self.copy_stream):
+            host_out["rgba"].copy_(self.rgba2[b], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.copy_stream)
+        self.copy_done[b] = ev
+        prev = self.copy_done[1 - b]
+        if prev is not None:
+            main.wait_event(prev)
+        self.frame += 1
 
     def roofline_terms(self, peaks, ktot, sms):
         return {}
