@@ -158,7 +158,7 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
     const float g_r = gRt, g_rs = Nf * gRu, g_rt = Nf * gRv;
     // table: the cell's corner weights go to the emitter (record index of corner (0,0) within the
     // glyph's texel table; corner (aa, bb) is record rec + bb P + aa)
-    emit((c.f * (N + 2) + j) * (N + 2) + i, A, B, s, t, g_r, g_rs, g_rt);
+    emit(((int64_t)c.f * (N + 2) + j) * (N + 2) + i, A, B, s, t, g_r, g_rs, g_rt);
     if (a.ddirs) {
         const float gs = g_r * rs + g_rs * rss + g_rt * rst;
         const float gt = g_r * rt + g_rs * rst + g_rt * rtt;

@@ -15,7 +15,7 @@ namespace shm {
 struct AtomicEmit {
     float4* dbase;
     int P;
-    __device__ __forceinline__ void operator()(int rec, const Herm2& A, const Herm2& B, float, float, float g_r,
+    __device__ __forceinline__ void operator()(int64_t rec, const Herm2& A, const Herm2& B, float, float, float g_r,
                                                float g_rs, float g_rt) const
     {
         float4 w[4];

@@ -33,7 +33,7 @@ struct DetEmit {
     uint64_t key;
     float* pay;  // [5][DBLOCK]: s, t, g_r, g_rs, g_rt
     int slot;
-    __device__ __forceinline__ void operator()(int rec, const Herm2&, const Herm2&, float s, float t, float g_r,
+    __device__ __forceinline__ void operator()(int64_t rec, const Herm2&, const Herm2&, float s, float t, float g_r,
                                                float g_rs, float g_rt)
     {
         key = ((uint64_t)rec << DBITS) | (uint64_t)slot;
