@@ -83,6 +83,11 @@ static shm_status same_resolutions(const shm_lut* a, const shm_lut* b, cudaStrea
     if (a->n_glyphs != b->n_glyphs) return SHM_ERR_INVALID_ARG;
     if (a->N_uniform > 0 || b->N_uniform > 0) return a->N_uniform == b->N_uniform ? SHM_OK : SHM_ERR_INVALID_ARG;
     if (a->N == b->N) return SHM_OK;
+    // per-glyph arrays are compared on the host, which needs a synchronisation: not possible while
+    // the stream is being captured into a graph, where the check is skipped
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return SHM_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SHM_OK;
     std::vector<int32_t> na(a->n_glyphs), nb(b->n_glyphs);
     if (cudaMemcpyAsync(na.data(), a->N, sizeof(int32_t) * na.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(nb.data(), b->N, sizeof(int32_t) * nb.size(), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
