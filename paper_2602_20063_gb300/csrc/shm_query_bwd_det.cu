@@ -12,22 +12,23 @@
 //   4. four passes, one per corner (aa, bb), add those sums to the slab with plain loads and stores:
 //      within one pass distinct cells write distinct records, and the passes are separated by CTA
 //      barriers, so every record receives its contributions in a fixed order.
-// Chunks run in order inside the CTA, glyphs are disjoint, so the whole result is fixed.  Small
-// uniform texel tables are staged in shared memory as in the atomic staged pass.
+// Chunks run in order inside the CTA, glyphs are disjoint, so the whole result is fixed.  Chunks of
+// 256 queries and four CTAs per SM (footprints read through L1/L2): with whole tables staged in
+// shared memory only two 1,024-thread CTAs fit per SM, which measured 5.7 ms against 4.7 ms on the
+// 2^26-query glyph field.
 #include "shm_bwd.cuh"
-#include "shm_stage.cuh"
 
 namespace shm {
 
 namespace {
 
-constexpr int DBLOCK = 1024;
-constexpr int DBITS = 10;  // log2(DBLOCK): query slot in the low bits of the sort key
+constexpr int DBLOCK = 256;
+constexpr int DBITS = 8;   // log2(DBLOCK): query slot in the low bits of the sort key
+constexpr int DMINB = 4;   // CTAs per SM
 constexpr uint64_t NO_KEY = ~0ull;
 
-// Shared memory after the (optional) staged table: two key buffers [DBLOCK] u64, then the payload
-// [5][DBLOCK] f32.
-constexpr uint32_t DET_SMEM_FIXED = 2 * DBLOCK * 8 + 5 * DBLOCK * 4;
+// Shared memory: two key buffers [DBLOCK] u64, then the payload [5][DBLOCK] f32.
+constexpr uint32_t DET_SMEM = 2 * DBLOCK * 8 + 5 * DBLOCK * 4;
 
 struct DetEmit {
     uint64_t key;
@@ -81,14 +82,11 @@ __device__ __forceinline__ uint64_t bitonic_sort(uint64_t x, uint64_t* buf0, uin
     return x;
 }
 
-template <int DT, int LAYOUT, bool STAGED>
-__global__ void __launch_bounds__(DBLOCK, 1) k_query_bwd_det(BackwardArgs a, uint32_t table_bytes)
+template <int DT, int LAYOUT>
+__global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ int s_abort;
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(smem);
-    const unsigned char* table = smem + stage::TABLE_OFFSET;
-    unsigned char* fixed = smem + (STAGED ? stage::TABLE_OFFSET + table_bytes : 0);
+    unsigned char* fixed = smem;
     uint64_t* kbuf0 = reinterpret_cast<uint64_t*>(fixed);
     uint64_t* kbuf1 = kbuf0 + DBLOCK;
     float* pay = reinterpret_cast<float*>(fixed + 2 * DBLOCK * 8);
@@ -110,29 +108,10 @@ __global__ void __launch_bounds__(DBLOCK, 1) k_query_bwd_det(BackwardArgs a, uin
             }
         }
     }
-    if (STAGED && tid == 0) {
-        stage::init(bar);
-        s_abort = 0;
-    }
-    __syncthreads();
-    uint32_t phase = 0;
     for (int g = blockIdx.x; g < G; g += gridDim.x) {
         const int64_t s0 = min(max(__ldg(a.seg + g), (int64_t)0), a.Q);
         const int64_t s1 = min(max(__ldg(a.seg + g + 1), s0), a.Q);
         if (s1 <= s0) continue;  // block-uniform
-        if (STAGED) {
-            if (tid == 0)
-                stage::issue(bar, bar + stage::TABLE_OFFSET,
-                             reinterpret_cast<const unsigned char*>(a.L.data) + (size_t)g * table_bytes, table_bytes);
-            if (!stage::bar_wait(bar, phase, stage::WAIT_NS)) s_abort = 1;
-            __syncthreads();
-            if (s_abort) {
-                status |= SHM_DEV_TIMEOUT;
-                if (tid == 0) stage::bar_wait(bar, phase, stage::DRAIN_NS);
-                break;
-            }
-            phase ^= 1;
-        }
         const GlyphRef Gr = glyph_ref(a.L, g);
         const int P = Gr.N + 2;
         float4* dbase = reinterpret_cast<float4*>(a.dlut) + glyph_ref(a.D, g).base;
@@ -145,15 +124,8 @@ __global__ void __launch_bounds__(DBLOCK, 1) k_query_bwd_det(BackwardArgs a, uin
                 const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
                 Chart c;
                 if (chart_of(d0, d1, d2, c)) {
-                    if (STAGED) {
-                        auto fetch = [table, P](int f, int i, int j) { return stage::corners<DT>(table, P, f, i, j); };
-                        bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
-                    } else {
-                        auto fetch = [&a, &Gr](int f, int i, int j) {
-                            return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j);
-                        };
-                        bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
-                    }
+                    auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
+                    bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
                 } else {
                     status |= SHM_DEV_NONFINITE;
                 }
@@ -201,38 +173,25 @@ __global__ void __launch_bounds__(DBLOCK, 1) k_query_bwd_det(BackwardArgs a, uin
                 __syncthreads();
             }
         }
-        if (STAGED) __syncthreads();  // every read of this table is done before the next copy lands
     }
     report_status(a.dev_status, status);
 }
 
-template <int DT, int LAYOUT, bool STAGED>
-cudaError_t launch_det_t(const BackwardArgs& a, uint32_t table_bytes, cudaStream_t s)
+template <int DT, int LAYOUT>
+cudaError_t launch_det_t(const BackwardArgs& a, cudaStream_t s)
 {
-    const int smem = (STAGED ? stage::TABLE_OFFSET + (int)table_bytes : 0) + (int)DET_SMEM_FIXED;
-    static int configured = -1;
-    if (configured != smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_det<DT, LAYOUT, STAGED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = (int)DET_SMEM;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_det<DT, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
+        configured = true;
     }
-    int64_t blocks = (int64_t)sm_count();
+    int64_t blocks = (int64_t)sm_count() * DMINB;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     if (blocks < 1) blocks = 1;
-    k_query_bwd_det<DT, LAYOUT, STAGED><<<(unsigned)blocks, DBLOCK, smem, s>>>(a, table_bytes);
+    k_query_bwd_det<DT, LAYOUT><<<(unsigned)blocks, DBLOCK, smem, s>>>(a);
     return cudaGetLastError();
-}
-
-template <int DT, int LAYOUT>
-cudaError_t launch_det_dl(const BackwardArgs& a, cudaStream_t s)
-{
-    if (LAYOUT == SHM_LAYOUT_TEXEL && a.L.N_uniform > 0) {
-        const int64_t P = (int64_t)a.L.N_uniform + 2;
-        const int64_t bytes = 6 * P * P * (DT == SHM_F32 ? 16 : 8);
-        if (bytes <= STAGED_TABLE_MAX_BYTES) return launch_det_t<DT, LAYOUT, true>(a, (uint32_t)bytes, s);
-    }
-    return launch_det_t<DT, LAYOUT, false>(a, 0, s);
 }
 
 }  // namespace
@@ -242,13 +201,13 @@ cudaError_t launch_query_bwd_det(const BackwardArgs& a, cudaStream_t s)
     if (a.Q == 0) return cudaSuccess;
     const int dt = a.L.dtype;
     if (a.L.layout == SHM_LAYOUT_TEXEL) {
-        if (dt == SHM_F32) return launch_det_dl<SHM_F32, SHM_LAYOUT_TEXEL>(a, s);
-        if (dt == SHM_F16) return launch_det_dl<SHM_F16, SHM_LAYOUT_TEXEL>(a, s);
-        return launch_det_dl<SHM_BF16, SHM_LAYOUT_TEXEL>(a, s);
+        if (dt == SHM_F32) return launch_det_t<SHM_F32, SHM_LAYOUT_TEXEL>(a, s);
+        if (dt == SHM_F16) return launch_det_t<SHM_F16, SHM_LAYOUT_TEXEL>(a, s);
+        return launch_det_t<SHM_BF16, SHM_LAYOUT_TEXEL>(a, s);
     }
-    if (dt == SHM_F32) return launch_det_dl<SHM_F32, SHM_LAYOUT_CELL>(a, s);
-    if (dt == SHM_F16) return launch_det_dl<SHM_F16, SHM_LAYOUT_CELL>(a, s);
-    return launch_det_dl<SHM_BF16, SHM_LAYOUT_CELL>(a, s);
+    if (dt == SHM_F32) return launch_det_t<SHM_F32, SHM_LAYOUT_CELL>(a, s);
+    if (dt == SHM_F16) return launch_det_t<SHM_F16, SHM_LAYOUT_CELL>(a, s);
+    return launch_det_t<SHM_BF16, SHM_LAYOUT_CELL>(a, s);
 }
 
 }  // namespace shm
