@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(QBLOCK, (QueryOccupancy<RECON, QBLOCK>::min_bl
             if (lane < 24) pv = __ldg(dirs4 + (3 * qw0) / 4 + lane);
         } else if (qw0 + lane < a.Q) {
             const int64_t q = qw0 + lane;
-            n0 = __ldg(a.dirs + 3 * q); n1 = __ldg(a.dirs + 3 * q + 1); n2 = __ldg(a.dirs + 3 * q + 2);
+            n0 = __ldcs(a.dirs + 3 * q); n1 = __ldcs(a.dirs + 3 * q + 1); n2 = __ldcs(a.dirs + 3 * q + 2);
         }
 #pragma unroll 1
         for (int it = 0; it < QIT; ++it) {
@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(QBLOCK, (QueryOccupancy<RECON, QBLOCK>::min_bl
                 if (VEC && qn + 32 <= a.Q) {
                     if (lane < 24) pv = __ldg(dirs4 + (3 * qn) / 4 + lane);
                 } else if (qn + lane < a.Q) {
-                    n0 = __ldg(a.dirs + 3 * (qn + lane));
-                    n1 = __ldg(a.dirs + 3 * (qn + lane) + 1);
-                    n2 = __ldg(a.dirs + 3 * (qn + lane) + 2);
+                    n0 = __ldcs(a.dirs + 3 * (qn + lane));
+                    n1 = __ldcs(a.dirs + 3 * (qn + lane) + 1);
+                    n2 = __ldcs(a.dirs + 3 * (qn + lane) + 2);
                 }
             }
             int gq = 0;
@@ -131,18 +131,18 @@ __global__ void __launch_bounds__(QBLOCK, (QueryOccupancy<RECON, QBLOCK>::min_bl
                 r.f = r.i = r.j = -1;
             }
             const Vec3 n = (a.normal && valid) ? surface_normal(d0, d1, d2, r.R, r.grad) : Vec3{qnan, qnan, qnan};
-            if (a.R) a.R[q] = r.R;
+            if (a.R) __stcs(a.R + q, r.R);
             if (full) {
                 if (a.grad) {
                     wb[3 * lane] = r.grad.x; wb[3 * lane + 1] = r.grad.y; wb[3 * lane + 2] = r.grad.z;
                     __syncwarp();
-                    if (lane < 24) reinterpret_cast<float4*>(a.grad)[(3 * qw) / 4 + lane] = reinterpret_cast<const float4*>(wb)[lane];
+                    if (lane < 24) __stcs(reinterpret_cast<float4*>(a.grad) + (3 * qw) / 4 + lane, reinterpret_cast<const float4*>(wb)[lane]);
                     __syncwarp();
                 }
                 if (a.normal) {
                     wb[3 * lane] = n.x; wb[3 * lane + 1] = n.y; wb[3 * lane + 2] = n.z;
                     __syncwarp();
-                    if (lane < 24) reinterpret_cast<float4*>(a.normal)[(3 * qw) / 4 + lane] = reinterpret_cast<const float4*>(wb)[lane];
+                    if (lane < 24) __stcs(reinterpret_cast<float4*>(a.normal) + (3 * qw) / 4 + lane, reinterpret_cast<const float4*>(wb)[lane]);
                     __syncwarp();
                 }
             } else {

@@ -8,7 +8,9 @@
 // of texel reads that miss L1 about half of the time.  Two CTAs per SM overlap one CTA's copy with
 // the other's queries.
 //
-// Results are bit-identical to k_query_fwd (same device functions on the same values).
+// Results are bit-identical to k_query_fwd (same device functions on the same values).  Directions
+// and outputs are touched once, so they are loaded and stored with the streaming cache hint
+// (__ldcs / __stcs: evict first) and leave L2 to the tables.
 // The wait for the copy is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, waits up to
 // 100 ms more for its copy to land and returns without touching the outputs of that glyph.
 #include "shm_stage.cuh"
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArg
         // first direction of this thread while the copy runs
         int64_t q = s0 + tid;
         float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-        if (q < s1) { d0 = __ldg(a.dirs + 3 * q); d1 = __ldg(a.dirs + 3 * q + 1); d2 = __ldg(a.dirs + 3 * q + 2); }
+        if (q < s1) { d0 = __ldcs(a.dirs + 3 * q); d1 = __ldcs(a.dirs + 3 * q + 1); d2 = __ldcs(a.dirs + 3 * q + 2); }
         if (!stage::bar_wait(bar, phase, stage::WAIT_NS)) s_abort = 1;
         __syncthreads();
         if (s_abort) {
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArg
         for (; q < s1; q += SBLOCK) {
             const int64_t qn = q + SBLOCK;
             float n0 = 0.f, n1 = 0.f, n2 = 0.f;
-            if (qn < s1) { n0 = __ldg(a.dirs + 3 * qn); n1 = __ldg(a.dirs + 3 * qn + 1); n2 = __ldg(a.dirs + 3 * qn + 2); }
+            if (qn < s1) { n0 = __ldcs(a.dirs + 3 * qn); n1 = __ldcs(a.dirs + 3 * qn + 1); n2 = __ldcs(a.dirs + 3 * qn + 2); }
             Chart c;
             float R = qnan, Ru = qnan, Rv = qnan;
             Vec3 grad{qnan, qnan, qnan}, nrm{qnan, qnan, qnan};
@@ -104,9 +106,9 @@ __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArg
             } else {
                 status |= SHM_DEV_NONFINITE;
             }
-            if (a.R) a.R[q] = R;
-            if (a.grad) { a.grad[3 * q] = grad.x; a.grad[3 * q + 1] = grad.y; a.grad[3 * q + 2] = grad.z; }
-            if (a.normal) { a.normal[3 * q] = nrm.x; a.normal[3 * q + 1] = nrm.y; a.normal[3 * q + 2] = nrm.z; }
+            if (a.R) __stcs(a.R + q, R);
+            if (a.grad) { __stcs(a.grad + 3 * q, grad.x); __stcs(a.grad + 3 * q + 1, grad.y); __stcs(a.grad + 3 * q + 2, grad.z); }
+            if (a.normal) { __stcs(a.normal + 3 * q, nrm.x); __stcs(a.normal + 3 * q + 1, nrm.y); __stcs(a.normal + 3 * q + 2, nrm.z); }
             if (a.chart) { a.chart[2 * q] = Ru; a.chart[2 * q + 1] = Rv; }
             if (a.fij) { a.fij[3 * q] = f; a.fij[3 * q + 1] = i; a.fij[3 * q + 2] = j; }
             d0 = n0; d1 = n1; d2 = n2;
