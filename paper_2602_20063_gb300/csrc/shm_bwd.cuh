@@ -116,13 +116,13 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
     const float iml = rsqrtf(ma * ma + mb * mb + mc * mc);
     const float na = ma * iml, nb = mb * iml, nc = mc * iml;
     // upstream in the (a, b, c) frame
-    float gRu_in = a.gR ? __ldg(a.gR + q) : 0.0f;
+    float gRu_in = a.gR ? __ldcs(a.gR + q) : 0.0f;
     float gGa = 0.f, gGb = 0.f, gGc = 0.f, gna = 0.f, gnb = 0.f, gnc = 0.f;
     if (FIT) {
         // L_q = w_v (R - R_t)^2 + w_n |n - n_t|^2: upstream dL/dR, dL/dn in the frame
-        const float eR = R - __ldg(a.R_target + q);
-        const float t0 = __ldg(a.n_target + 3 * q), t1 = __ldg(a.n_target + 3 * q + 1),
-                    t2 = __ldg(a.n_target + 3 * q + 2);
+        const float eR = R - __ldcs(a.R_target + q);
+        const float t0 = __ldcs(a.n_target + 3 * q), t1 = __ldcs(a.n_target + 3 * q + 1),
+                    t2 = __ldcs(a.n_target + 3 * q + 2);
         const float ea = na - pick3(c.k, t0, t1, t2) * c.sigma, eb = nb - pick3(c.k1, t0, t1, t2),
                     ec = nc - pick3(c.k2, t0, t1, t2);
         loss_acc += a.w_value * eR * eR + a.w_normal * (ea * ea + eb * eb + ec * ec);
@@ -132,13 +132,13 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
         gnc = 2.0f * a.w_normal * ec;
     }
     if (!FIT && a.ggrad) {
-        const float gx0 = __ldg(a.ggrad + 3 * q), gx1 = __ldg(a.ggrad + 3 * q + 1), gx2 = __ldg(a.ggrad + 3 * q + 2);
+        const float gx0 = __ldcs(a.ggrad + 3 * q), gx1 = __ldcs(a.ggrad + 3 * q + 1), gx2 = __ldcs(a.ggrad + 3 * q + 2);
         gGa = pick3(c.k, gx0, gx1, gx2) * c.sigma;
         gGb = pick3(c.k1, gx0, gx1, gx2);
         gGc = pick3(c.k2, gx0, gx1, gx2);
     }
     if (!FIT && a.gnormal) {
-        const float gx0 = __ldg(a.gnormal + 3 * q), gx1 = __ldg(a.gnormal + 3 * q + 1), gx2 = __ldg(a.gnormal + 3 * q + 2);
+        const float gx0 = __ldcs(a.gnormal + 3 * q), gx1 = __ldcs(a.gnormal + 3 * q + 1), gx2 = __ldcs(a.gnormal + 3 * q + 2);
         gna = pick3(c.k, gx0, gx1, gx2) * c.sigma;
         gnb = pick3(c.k1, gx0, gx1, gx2);
         gnc = pick3(c.k2, gx0, gx1, gx2);

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(BBLOCK, 4) k_query_bwd(BackwardArgs a)
                 gq = g;
             }
             float3 dd = make_float3(qnan, qnan, qnan);
-            const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
+            const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
             Chart c;
             bool ok = (gq >= 0 && gq < G);
             if (!ok) status |= SHM_DEV_BOUNDS;
@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(BBLOCK, 4) k_query_bwd(BackwardArgs a)
                 bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
             }
             if (a.ddirs) {
-                a.ddirs[3 * q] = dd.x;
-                a.ddirs[3 * q + 1] = dd.y;
-                a.ddirs[3 * q + 2] = dd.z;
+                __stcs(a.ddirs + 3 * q, dd.x);
+                __stcs(a.ddirs + 3 * q + 1, dd.y);
+                __stcs(a.ddirs + 3 * q + 2, dd.z);
             }
         }
     }
@@ -143,11 +143,11 @@ __global__ void __launch_bounds__(SBB, 2) k_query_bwd_staged(BackwardArgs a, uin
         AtomicEmit sink{dbase, P};
         for (int64_t q = s0 + tid; q < s1; q += SBB) {
             float3 dd = make_float3(qnan, qnan, qnan);
-            const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
+            const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
             Chart c;
             if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
             else status |= SHM_DEV_NONFINITE;
-            if (a.ddirs) { a.ddirs[3 * q] = dd.x; a.ddirs[3 * q + 1] = dd.y; a.ddirs[3 * q + 2] = dd.z; }
+            if (a.ddirs) { __stcs(a.ddirs + 3 * q, dd.x); __stcs(a.ddirs + 3 * q + 1, dd.y); __stcs(a.ddirs + 3 * q + 2, dd.z); }
         }
         __syncthreads();  // every read of this table is done before the next copy lands
     }

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
             DetEmit emit{NO_KEY, pay, tid};
             if (q < s1) {
                 float3 dd = make_float3(qnan, qnan, qnan);
-                const float d0 = __ldg(a.dirs + 3 * q), d1 = __ldg(a.dirs + 3 * q + 1), d2 = __ldg(a.dirs + 3 * q + 2);
+                const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
                 Chart c;
                 if (chart_of(d0, d1, d2, c)) {
                     auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
                 } else {
                     status |= SHM_DEV_NONFINITE;
                 }
-                if (a.ddirs) { a.ddirs[3 * q] = dd.x; a.ddirs[3 * q + 1] = dd.y; a.ddirs[3 * q + 2] = dd.z; }
+                if (a.ddirs) { __stcs(a.ddirs + 3 * q, dd.x); __stcs(a.ddirs + 3 * q + 1, dd.y); __stcs(a.ddirs + 3 * q + 2, dd.z); }
             }
             // 2. group by cell, queries in order within a cell (the payload writes are ordered before
             //    the reads of step 3 by the sort's barriers)
