@@ -9,7 +9,8 @@
 // Child directions outside the face, on the gutter ring and the one-texel bake margin, are
 // ordinary queries that land on the neighbouring face, so the seam treatment of the fine level is
 // inherited.  Inside the face a child sits exactly on a fine texel centre, where the interpolant
-// equals the stored value.
+// equals the stored value (§3.3): the four children of an interior coarse texel are the corners of
+// fine cell (2ic-1, 2jc-1), read with one footprint fetch and no interpolation.
 //
 // One CTA per (16 x 16 coarse-texel tile, face, glyph): 18 x 18 margin samples (4 fine queries
 // each, value only) into shared memory, then one record per thread, stored in any dtype/layout.
@@ -43,7 +44,11 @@ __global__ void __launch_bounds__(256) k_mip(LutView fine, LutView coarse, void*
     for (int e = tid; e < MS * MS; e += 256) {
         const int ii = i0 + (e % MS), jj = j0 + (e / MS);
         float acc = 0.0f;
-        if (paired && ii < S && jj < S) {
+        const int ic = ii - 1, jc = jj - 1;
+        if (paired && ii < S && jj < S && ic >= 1 && ic <= Nc && jc >= 1 && jc <= Nc) {
+            const Corners cr = fetch_corners<DT, LAYOUT>(fine.data, Gf, f, 2 * ic - 1, 2 * jc - 1);
+            acc = 0.25f * (((cr.c00.x + cr.c10.x) + cr.c01.x) + cr.c11.x) + dr0;
+        } else if (paired && ii < S && jj < S) {
             // sample (ii, jj) is coarse texel (ii-1, jj-1); its children are fine texels
             // 2(ii-1)-1+a, a in {0, 1}, at 2u-1 = (2 i_f - 1 - Nf)/Nf
             for (int b = 0; b < 2; ++b) {
