@@ -802,7 +802,8 @@ class Planet:
                            "level1_achieved_GBps": round(gbs, 1),
                            "level1_frac_of_measured_hbm": round(gbs / load_peaks()["hbm_gbs"], 3),
                            "per_unit": "algorithmic 16 B read per fine texel + 16 B written per coarse texel "
-                                       "(each coarse sample = 4 fine interpolant values, L1/L2-served)"}
+                                       "(interior coarse samples: the mean of their four children's stored values; "
+                                       "gutter and margin rings: four fine interpolant queries)"}
         del chain
         return ex
 
