@@ -690,7 +690,9 @@ class Planet:
                                "per_unit": f"{per_q} B/query (no-reuse accounting; neighbouring pixels share texels, "
                                            "so L2 serves most table reads)", "files": qfiles},
             "fbm_bake": {"bound": "hbm", "algorithmic": T * 16, "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                         "per_unit": "16 B written per texel (8 octaves x 8 PCG3D lattice hashes per sample: ALU-heavy)",
+                         "per_unit": "16 B written per texel (8 octaves x 8 PCG3D lattice hashes per sample); the "
+                                     "kernel is issue-bound, not DRAM-bound: ncu shows issue slots 88 % and DRAM 5 % busy "
+                                     "(profiles/fd_face_fbm_planet.md)",
                          "files": ["paper_2602_20063_gb300/csrc/shm_build.cu"]},
         }
 
