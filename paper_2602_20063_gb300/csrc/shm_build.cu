@@ -516,11 +516,16 @@ __global__ void __launch_bounds__(256) k_value_build(LutView out, void* data, sh
 // needs 18x18 samples, up to 3.2x the face's count at N = 16); larger tables use 64x64 regions
 // (6 % re-evaluation at the region borders).  Pools of uneven N cap the region at FACE_SPLIT_T
 // texels: a face of N = 128 then takes four CTAs, so the largest faces no longer set the launch's
-// tail, and the smaller shared-memory footprint lets five CTAs share an SM instead of three.  The
-// sample directions and values are those of the value tables (k_value_build).
+// tail, and the smaller shared-memory footprint lets five CTAs share an SM instead of three.
+// Uniform pools split each face into 2 x 2 equal regions once a whole face's samples would need
+// more than FACE_SPLIT_SMEM bytes, i.e. fewer CTAs per SM than the register limit of five allows
+// (512 bump objects: N = 128 0.944 vs 0.982 ms, N = 144 1.171 vs 1.340 ms; N <= 96 stays whole,
+// where splitting measured -1 % to +1 %).  The sample directions and values are those of the
+// value tables (k_value_build).
 constexpr int FACE_N_MAX = 144;   // (N+4)^2 floats <= 87.6 KB
 constexpr int REGION_T = 64;      // region edge for larger tables: 66^2 floats = 17.4 KB
 constexpr int FACE_SPLIT_T = 66;  // uneven pools: N <= 64 faces stay whole, N = 128 faces split 2 x 2
+constexpr int FACE_SPLIT_SMEM = 45 * 1024;
 
 // FBM: the fBm source (its lattice cache is only allocated in that instantiation); otherwise stored
 // samples or Gaussian bumps.
@@ -695,6 +700,8 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
     {
         int T = (sz.max_N <= FACE_N_MAX) ? sz.max_N + 2 : REGION_T;
         if (sz.N_uniform == 0 && T > FACE_SPLIT_T) T = FACE_SPLIT_T;
+        if (sz.N_uniform > 0 && T <= FACE_N_MAX + 2 && (T + 2) * (T + 2) * (int)sizeof(float) > FACE_SPLIT_SMEM)
+            T = (T + 1) / 2;
         const int smem = (T + 2) * (T + 2) * (int)sizeof(float);
         static int configured[2][2] = {{0, 0}, {0, 0}};
         const int mi = sz.N_uniform > 0 ? 0 : 1, fi = src.kind == SHM_SRC_FBM ? 1 : 0;

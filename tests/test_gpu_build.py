@@ -200,6 +200,42 @@ def test_fd_build_bumps(S):
     print("bumps: worst record error / eps_S =", worst)
 
 
+@pytest.mark.parametrize("N", [96, 104, 144])
+def test_fd_build_bumps_uniform(S, N):
+    """Uniform pools whole-face (N = 96) and split into 2 x 2 regions (N = 104: 53-texel regions,
+    N = 144: 73) give the oracle's records within the float32 bound of the bump sum."""
+    counts, offs, mu, amp, width = I.bump_params(3, 91 + N)
+    lut = S.alloc_lut(3, N, r0=[1.0] * 3)
+    mu32, amp32, w32 = mu.astype(np.float32), amp.astype(np.float32), width.astype(np.float32)
+    src = S.Source(kind=S.SHM_SRC_BUMPS, bump_offset=torch.from_numpy(offs).cuda(),
+                   mu=torch.from_numpy(mu32).cuda(), amp=torch.from_numpy(amp32).cuda(),
+                   width=torch.from_numpy(w32).cuda())
+    S.build_lut(lut, src)
+    got = lut.data.cpu().numpy().astype(np.float64).reshape(3, 6, N + 2, N + 2, 4)
+    for g in range(3):
+        s = slice(offs[g], offs[g + 1])
+        samples = O.sample_grid_bumps(N, mu32[s].astype(np.float64), amp32[s].astype(np.float64),
+                                      w32[s].astype(np.float64))
+        ref = O.bake_fd(N, samples, r0=1.0)
+        eps_S = 8 * 2.0 ** -24 * np.abs(amp32[s]).sum()
+        err = np.abs(got[g] - ref).max(axis=(0, 1, 2))
+        assert np.all(err <= 2 * eps_S), (g, err, eps_S)
+
+
+def test_fd_build_fbm_split(S):
+    """fBm at N = 128 (faces split into 2 x 2 regions of 65 texels, directions divided per sample)."""
+    N = 128
+    keys = I.fbm_keys(12)
+    lut = S.alloc_lut(1, N, r0=[1.0])
+    src = S.Source(kind=S.SHM_SRC_FBM, octaves=8, keys=torch.from_numpy(keys.view(np.int32)).cuda(),
+                   base_freq=2.0, lacunarity=2.0, gain=0.5, amplitude=0.02)
+    S.build_lut(lut, src)
+    got = lut.data.cpu().numpy().astype(np.float64).reshape(6, N + 2, N + 2, 4)
+    ref = O.bake_fd(N, O.sample_grid_fbm(N, keys, 2.0, 2.0, 0.5, 0.02), r0=0.0)
+    err = np.abs(got - ref).max(axis=(0, 1, 2))
+    assert np.all(err <= 2 * 4e-8), err
+
+
 def test_fd_build_fbm(S):
     N = 64
     keys = I.fbm_keys(11)
