@@ -2,12 +2,28 @@
 // to the kernel launchers, CUDA error mapping.  No device memory is allocated here.
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <vector>
 
 #include "shm_internal.h"
 
 namespace shm {
+
+cudaError_t ensure_dynamic_smem(const void* fn, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> set;  // (kernel, device) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int& cur = set[{fn, dev}];
+    if (cur >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 int sm_count()
 {

@@ -503,12 +503,8 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     a.out = reinterpret_cast<float*>(data);
     a.direct = direct ? 1 : 0;
     a.dev_status = dev_status;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(tc::k_sh_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return attr_err;
+    e = ensure_dynamic_smem((const void*)tc::k_sh_gemm_tc, (int)tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     const int tiles = ((M + tc::TM - 1) / tc::TM) * ((G + tc::TN - 1) / tc::TN);
     int grid = sm_count();
     if (grid > tiles) grid = tiles;

@@ -703,18 +703,12 @@ cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& sr
         if (sz.N_uniform > 0 && T <= FACE_N_MAX + 2 && (T + 2) * (T + 2) * (int)sizeof(float) > FACE_SPLIT_SMEM)
             T = (T + 1) / 2;
         const int smem = (T + 2) * (T + 2) * (int)sizeof(float);
-        static int configured[2][2] = {{0, 0}, {0, 0}};
         const int mi = sz.N_uniform > 0 ? 0 : 1, fi = src.kind == SHM_SRC_FBM ? 1 : 0;
-        if (configured[fi][mi] < smem) {
-            auto attr = [smem](const void* fn) {
-                return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            };
-            cudaError_t e = fi ? (mi == 0 ? attr((const void*)k_fd_face<true, UniformMap>)
-                                          : attr((const void*)k_fd_face<true, TileMap>))
-                               : (mi == 0 ? attr((const void*)k_fd_face<false, UniformMap>)
-                                          : attr((const void*)k_fd_face<false, TileMap>));
+        {
+            const void* fn = fi ? (mi == 0 ? (const void*)k_fd_face<true, UniformMap> : (const void*)k_fd_face<true, TileMap>)
+                                : (mi == 0 ? (const void*)k_fd_face<false, UniformMap> : (const void*)k_fd_face<false, TileMap>);
+            cudaError_t e = ensure_dynamic_smem(fn, smem);
             if (e != cudaSuccess) return e;
-            configured[fi][mi] = smem;
         }
         auto regions = [T](int N) {
             const int64_t r = (N + 2 + T - 1) / T;

@@ -126,6 +126,11 @@ struct BackwardArgs {
 
 int sm_count();
 
+// Raises kernel fn's dynamic shared-memory limit to at least `bytes` on the calling thread's
+// current device.  The attribute belongs to the device's context, so it is tracked per (kernel,
+// device); thread-safe.
+cudaError_t ensure_dynamic_smem(const void* fn, int bytes);
+
 cudaError_t launch_query_fwd(const QueryArgs& a, cudaStream_t s);
 cudaError_t launch_query_bwd_det(const BackwardArgs& a, cudaStream_t s);
 // Glyph tables up to this size are staged whole in shared memory by the segment query (two CTAs

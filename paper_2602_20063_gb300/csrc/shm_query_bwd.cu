@@ -162,13 +162,8 @@ template <int DT, bool FIT>
 static cudaError_t launch_bwd_staged_ft(const BackwardArgs& a, uint32_t table_bytes, cudaStream_t s)
 {
     const int smem = stage::TABLE_OFFSET + (int)table_bytes;
-    static int configured = -1;
-    if (configured != smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_staged<DT, FIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = ensure_dynamic_smem((const void*)k_query_bwd_staged<DT, FIT>, smem);
+    if (e != cudaSuccess) return e;
     int64_t blocks = (int64_t)sm_count() * 2;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     k_query_bwd_staged<DT, FIT><<<(unsigned)blocks, SBB, smem, s>>>(a, table_bytes);

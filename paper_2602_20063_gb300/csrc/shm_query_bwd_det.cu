@@ -181,12 +181,8 @@ template <int DT, int LAYOUT>
 cudaError_t launch_det_t(const BackwardArgs& a, cudaStream_t s)
 {
     const int smem = (int)DET_SMEM;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_query_bwd_det<DT, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = ensure_dynamic_smem((const void*)k_query_bwd_det<DT, LAYOUT>, smem);
+    if (e != cudaSuccess) return e;
     int64_t blocks = (int64_t)sm_count() * DMINB;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     if (blocks < 1) blocks = 1;

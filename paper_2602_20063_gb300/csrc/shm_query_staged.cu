@@ -122,12 +122,8 @@ template <int DT, int SBLOCK>
 cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
 {
     const int smem = stage::TABLE_OFFSET + (int)table_bytes;
-    static int configured = -1;
-    if (configured != smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_query_staged<DT, SBLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = ensure_dynamic_smem((const void*)k_query_staged<DT, SBLOCK>, smem);
+    if (e != cudaSuccess) return e;
     int resident = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT, SBLOCK>, SBLOCK, smem) != cudaSuccess ||
         resident < 1)
