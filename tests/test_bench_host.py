@@ -35,6 +35,16 @@ def test_traffic_is_dropped_when_the_kernel_source_changes(bench):
     assert bench.load_traffic("no_such_kernel", e["files"]) is None
 
 
+def test_committed_traffic_matches_the_current_kernels(bench):
+    """The DRAM traffic the bench reports was captured on the kernel sources in the tree: a kernel
+    edited without a new capture fails here instead of reporting traffic: null."""
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        d = json.load(f)
+    for kernel, e in d.items():
+        assert e["source_hash"] == bench.source_hash(*e["files"]), kernel
+        assert os.path.exists(os.path.join(ROOT, e["profile"])), kernel
+
+
 def test_clock_record_flags_throttling(bench, tmp_path):
     cs = bench.ClockSampler(0)
     path = tmp_path / "clocks.csv"
