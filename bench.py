@@ -834,7 +834,7 @@ class Planet:
         """Oracle rate projected to one planet step: per-process FD bake rate (N = 128 faces) and query
         rate (2^14 queries), times the process count, applied to 6 x 2050^2 texels + 2^29 queries."""
         with _PoolScope(pool, procs) as pool:
-            res = pool.map(_oracle_planet_task, self.oracle_task_args(procs))
+            res = pool.map(_oracle_planet_task, [a + (128, 16384) for a in self.oracle_task_args(procs)])
         texels, tb, q, tq = (np.array([r[i] for r in res], dtype=np.float64) for i in range(4))
         bake_rate = procs * texels.mean() / tb.mean()
         query_rate = procs * q.mean() / tq.mean()
@@ -849,19 +849,19 @@ class Planet:
 
 
 def _oracle_planet_task(args):
-    """Oracle sample of the planet step: bake N = 128 faces (rate per texel) and 2^14 queries."""
-    kind, k, keys, seed = args
+    """Oracle sample of the planet step: bake Nb faces (rate per texel) and nq queries."""
+    kind, k, keys, seed, Nb, nq = args
     import oracle as O
     import shm_inputs as I
     t0 = time.perf_counter()
-    samples = O.sample_grid_fbm(128, keys, 2.0, 2.0, 0.5, 0.02)
-    lut = O.bake_fd(128, samples)
+    samples = O.sample_grid_fbm(Nb, keys, 2.0, 2.0, 0.5, 0.02)
+    lut = O.bake_fd(Nb, samples)
     t1 = time.perf_counter()
     pool, off, Ns = O.make_pool([lut])
-    d = I.directions_range(k * 16384, 16384, seed + 11)
+    d = I.directions_range(k * nq, nq, seed + 11)
     O.query(pool, off, Ns, d, r0=np.array([1.0]), nthreads=1)
     t2 = time.perf_counter()
-    return (6 * 130 * 130, t1 - t0, 16384, t2 - t1)
+    return (6 * (Nb + 2) ** 2, t1 - t0, nq, t2 - t1)
 
 
 class Impostors:
@@ -1200,12 +1200,13 @@ class Fit:
     def oracle_measure(self, budget_s, procs, pool=None):
         """Oracle rate: FP64 loss + adjoint of 4,096 queries on one N = 64 glyph per process, plus Adam
         over that glyph's table, projected to one step (1,024 glyphs, 2^24 queries)."""
+        nq = 4096  # queries per process
         with _PoolScope(pool, procs) as pool:
-            res = pool.map(_oracle_fit_task, [(k, self.coeffs[k], self.seed) for k in range(procs)])
-        tq = np.mean([r[0] for r in res]) / 4096.0
+            res = pool.map(_oracle_fit_task, [(k, self.coeffs[k], self.seed, nq) for k in range(procs)])
+        tq = np.mean([r[0] for r in res]) / nq
         ta = np.mean([r[1] for r in res])
         t_step = (self.Q * tq + self.G * ta) / procs
-        return self.Q / t_step, (f"{procs} processes each: FP64 loss + adjoint of 4,096 queries and Adam over one "
+        return self.Q / t_step, (f"{procs} processes each: FP64 loss + adjoint of {nq:,} queries and Adam over one "
                                  "N = 64 glyph table, projected to 2^24 queries + 1,024 tables")
 
     def oracle_task_args(self, n, start=0):
@@ -1213,7 +1214,7 @@ class Fit:
 
 
 def _oracle_fit_task(args):
-    k, c, seed = args
+    k, c, seed, nq = args
     import oracle as O
     import oracle.fit as OF
     import shm_inputs as I
@@ -1221,7 +1222,7 @@ def _oracle_fit_task(args):
     lut = np.zeros((6, N + 2, N + 2, 4))
     lut[..., 0] = c[0] * 0.28209479177387814
     pool, off, Ns = O.make_pool([lut])
-    d = I.directions_range(k * 4096, 4096, seed + 100)
+    d = I.directions_range(k * nq, nq, seed + 100)
     Rt, _, nt = O.sh_eval(L, c.astype(np.float64), d, nthreads=1)
     t0 = time.perf_counter()
     loss, g = OF.loss_and_grad(pool, off, Ns, d, Rt, nt)
