@@ -16,7 +16,9 @@
 // Schedule: persistent CTAs (one per SM, 256 threads), tiles of 128 columns x 256 glyphs, K in
 // chunks of 16 (64 B rows, 64-byte swizzle), 3 smem stages of 48 KB so TMA runs chunks ahead of
 // the MMAs, 2 TMEM accumulators of 256 columns (512 columns, the whole TMEM) so the epilogue of
-// one tile overlaps the MMAs of the next.
+// one tile overlaps the MMAs of the next.  CTA b takes tiles b, b + grid, ..., with the glyph tile
+// varying fastest, so the CTAs running together share column tiles of the basis (1.3 % faster than
+// column tiles fastest; contiguous runs of tiles per CTA were 11 % slower).
 //   warp 0 lane 0: TMA producer        warp 1: TMEM allocation; lane 0 issues the MMAs
 //   warps 4-7: epilogue (TMEM lane quadrant = warp % 4), table writes
 // Epilogue of the float32 texel table: per 32 glyphs the four warps transpose their TMEM rows into
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(256, 1)
         uint32_t it = 0;  // chunks issued so far
         bool ok = true;
         for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-            const int mt = t % num_m, nt = t / num_m;
+            const int nt = t % num_n, mt = t / num_n;
             for (int c = 0; c < NC; ++c, ++it) {
                 const int s = it % NSTAGE;
                 const uint32_t ph = (it / NSTAGE) & 1;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(256, 1)
         const bool issuer = (warp == 4 && lane == 0);
         uint32_t j = 0, box = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
-            const int mt = t % num_m, nt = t / num_m;
+            const int nt = t % num_n, mt = t / num_n;
             const uint32_t acc = j & 1, aph = (j >> 1) & 1;
             const bool ok = mbar_wait(tfull0 + 8 * acc, aph, abort_flag, WAIT_LIMIT_NS);
             if (a.direct) {
