@@ -135,6 +135,33 @@ shm_status shm_tune_query(const shm_lut* lut, int64_t Q, const float* dirs, cons
                           int32_t* chosen, float* times_ms, shm_stream stream);
 shm_status shm_tune_reset(void);
 
+/* Binned query of one large table in random order (no counterpart in the paper, whose fragment
+ * shader reads each footprint through the texture cache; the workload is the procedural planet of
+ * §4.10 queried at uniformly random directions).  Same per-query results as shm_query with
+ * glyph = seg = NULL (every query on glyph 0): R [Q], grad [Q][3], normal [Q][3] and the chart
+ * derivatives chart [Q][2] (R_u, R_v), each may be NULL, in query order, bit-identical to
+ * shm_query's.  Work: the queries are partitioned by the table region their 2x2 footprint reads
+ * -- face and band of cell rows, a band holding about band_bytes of records (0 = 32 MiB) -- the
+ * query runs over the partitioned batch so that the bands in flight stay resident in L2, and the
+ * results return to query order.  The partition is stable and computed on the device; nothing is
+ * synchronised with the host.
+ *   - lut: any dtype, texel or cell layout, uniform resolution (N_uniform > 0, else
+ *     SHM_ERR_UNSUPPORTED); only glyph 0 is read.
+ *   - ws: device workspace of at least shm_query_binned_workspace_bytes(lut, Q, band_bytes)
+ *     (about 25 B per query: the partitioned directions, intermediate R / R_u / R_v, one bin byte
+ *     per query and per-tile counts), else SHM_ERR_WORKSPACE.  Its contents need no clearing and
+ *     are scratch after the call; two calls that overlap on the GPU must not share it.
+ *   - dirs and the outputs follow shm_query's rules (device or page-locked host memory); the
+ *     directions are read three times, so device memory is the fast case.
+ *   - band_bytes < 0 or Q < 0: SHM_ERR_INVALID_ARG. */
+int64_t shm_query_binned_workspace_bytes(const shm_lut* lut, int64_t Q, int64_t band_bytes);
+/* Bins (6 faces x bands) the partition uses for (lut, band_bytes); *band_rows (host, may be NULL)
+ * receives the cell rows per band.  -1 for an unsupported table. */
+int32_t shm_query_binned_bins(const shm_lut* lut, int64_t band_bytes, int32_t* band_rows);
+shm_status shm_query_binned(const shm_lut* lut, int64_t Q, const float* dirs, float* R, float* grad,
+                            float* normal, float* chart, int64_t band_bytes, void* ws, size_t ws_bytes,
+                            int32_t* dev_status, shm_stream stream);
+
 /* Value-only reconstruction baselines (§4.2 Table psnr_value, §4.5 Table cost_extended) on a
  * SHM_LAYOUT_VALUE table, with the chart, glyph selection, outputs and status rules of shm_query.
  * With x = uN + 1/2 (texel i at x = i) and (i, s) the cell of x as in shm_query:
@@ -359,7 +386,9 @@ shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj
  *     shm_raycast_workspace_bytes(n_obj, W, H) exceeds it return SHM_ERR_WORKSPACE and launch
  *     nothing (512 objects at 1920x1080 fit).
  *   - The first call on a device looks up the array's device address (with that device current)
- *     and caches it; make that first call before any stream capture on the device.
+ *     and caches it per device index for the life of the process; make that first call before any
+ *     stream capture on the device.  A cudaDeviceReset of that device invalidates the cached
+ *     address: do not call this entry point again in that process after such a reset.
  *   - All calls share the one array, which keeps the previous call's contents (the counters that
  *     must start at zero are cleared on `stream` by every call).  Calls that overlap on the GPU,
  *     for example on two streams, race on it: serialise them.
@@ -369,15 +398,7 @@ shm_status shm_raycast_noalloc(const shm_lut* lut, const shm_object* objs, int32
                                float* depth, float* normal, int32_t* obj_id, int32_t* dev_status,
                                shm_stream stream);
 
-/* ---------------------------------------------------------------- measurement aid (not in the paper) */
-
-/* Random-gather ceiling: the memory traffic of an uncorrelated query batch without its
- * arithmetic, to measure what the memory system sustains for that access pattern.  For each
- * q < Q: reads in[3q..3q+2] (12 B), gathers one block_bytes block (16, 32, 48 or 64; 16-byte
- * aligned `table` of table_bytes) at a position hashed from those three values, writes
- * out[7q..7q+6] (28 B).  The values written are meaningless. */
-shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t block_bytes, int64_t Q,
-                            const float* in, float* out, shm_stream stream);
+/* ---------------------------------------------------------------- L2 hint (not in the paper) */
 
 /* L2 fetch granularity of the calling thread's current device context (a CUDA context limit,
  * released with the context; no device setting outlives the process): the largest block the L2

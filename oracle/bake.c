@@ -1,10 +1,10 @@
 /*
- * Oracle (test infrastructure only): Algorithm 1, "Bake-time Spherical Hermite Map (per face)".
+ * Oracle (test infrastructure only): Algorithm 1 (the per-face bake), §3.3.
  *
  * For every stored texel centre (u_i, v_j) of the padded (N+2)^2 face, gutter included, the
  * record (r, r_u h, r_v h, r_uv h^2) with h = 1/N is stored (Eq. hermite_storage).  Gutter
  * texels are filled by evaluating the function at their own centres in the face's own chart,
- * never by copying or reflecting (§3.2).  Two derivative modes (§3.3 "Derivative computation"):
+ * never by copying or reflecting (§3.2).  Two derivative modes (§3.3):
  *   analytic SH   exact chart derivatives of the SH expansion (sh.c, hyper-dual);
  *   finite diff.  central differences in (u,v) on a sample grid that carries a one-texel
  *                 bake-time margin beyond the gutter (the paper allows a margin or one-sided

@@ -1,16 +1,16 @@
 /*
  * Oracle (test infrastructure only): cubemap chart, tangents, metric and normal in float64.
  *
- * §3.2 "Padded Cubemap Parameterization": a direction maps to one of six faces with local
- * (u,v) in [0,1]^2.  The paper prints no face table, so this file fixes one (any fixed table
- * is correct because gutters are baked by evaluation in each face's own chart, §3.2):
+ * §3.2: a direction maps to one of six faces with local (u,v) in [0,1]^2.  The paper prints
+ * no face table, so this file fixes one (any fixed table is correct because gutters are baked
+ * by evaluation in each face's own chart, §3.2):
  *   axis k = argmax_k |w_k| (ties -> lowest k), sign sigma = +1 iff w_k >= 0 (so -0 counts as +),
  *   face f = 2k + (sigma < 0); frame a_f = sigma e_k, b_f = e_{(k+1)%3}, c_f = e_{(k+2)%3};
  *   unnormalised direction w~(u,v) = a_f + (2u-1) b_f + (2v-1) c_f.
  * §3.2 texel centres: padded (N+2)^2 per face, interior 1..N, h = 1/N; the paper does not say
  * where centres lie; the cell-centred reading u_i = (i - 1/2)/N is used (gutter i=0 at -h/2).
- * §3.4 "Analytic Normals from Chart Derivatives": tangents by differentiating the normalised
- * cubemap direction, metric tensor G, Cramer's rule, clamped det G, normal n.
+ * §3.4: tangents by differentiating the normalised cubemap direction, metric tensor G, Cramer's
+ * rule, clamped det G, normal n.
  */
 #include <math.h>
 #include "oracle.h"

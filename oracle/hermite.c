@@ -1,5 +1,5 @@
 /*
- * Oracle (test infrastructure only): §3.3 "Reconstruction" and "Derivative extraction".
+ * Oracle (test infrastructure only): §3.3 (reconstruction and derivative extraction).
  *
  * 1-D cubic Hermite basis (§3.3):  H0 = 2s^3 - 3s^2 + 1,  H1 = -2s^3 + 3s^2,
  *                                   H0d = s^3 - 2s^2 + s,  H1d = s^3 - s^2.

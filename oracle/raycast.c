@@ -1,5 +1,5 @@
 /*
- * Oracle (test infrastructure only): §3.1 "Surface Model and Billboard Rendering" in float64.
+ * Oracle (test infrastructure only): §3.1 (surface model and ray casting) in float64.
  *
  * Surface x(w) = c + R(w) w with R = s |r| (s > 0 the object scale); implicit
  * F(x) = |x - c| - R(w), w = (x - c)/|x - c|.  Per pixel a view ray p(t) = o + t d is cast;

@@ -1,7 +1,7 @@
 /*
  * Oracle (test infrastructure only): real spherical harmonics with exact chart derivatives.
  *
- * §3.3 "Analytic SH derivatives": r(w) = sum_{l,m} c_l^m Y_l^m(w); derivatives of the SH
+ * §3.3 (analytic SH derivatives): r(w) = sum_{l,m} c_l^m Y_l^m(w); derivatives of the SH
  * expansion are exact, and are converted to face-chart (u,v) derivatives by the chain rule.
  * The paper fixes neither normalisation, phase nor indexing.  Reading used here:
  *   orthonormal real SH on S^2, coefficient index k = l*l + l + m, no Condon-Shortley phase,

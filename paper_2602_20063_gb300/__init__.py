@@ -10,8 +10,8 @@ from .binding import (  # noqa: F401
     SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM,
     SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT, SHM_BWD_DETERMINISTIC,
     Lut, Source, ShmError, alloc_lut, like_lut, lib, lib_path,
-    query, query_recon, tune_query, tune_reset, sh_basis, build_lut, build_workspace, build_workspace_bytes, pack_lut, lut_bounds, build_mip, mip_like, mip_chain, query_backward, build_lut_backward, sh_eval, fit_backward, adam_step,
+    query, query_binned, query_binned_workspace, query_binned_workspace_bytes, query_binned_bins, query_recon, tune_query, tune_reset, sh_basis, build_lut, build_workspace, build_workspace_bytes, pack_lut, lut_bounds, build_mip, mip_like, mip_chain, query_backward, build_lut_backward, sh_eval, fit_backward, adam_step,
     make_camera, make_raycast_params, objects_tensor, raycast, raycast_noalloc, raycast_workspace_bytes, raycast_query_count,
-    records_per_glyph, record_bytes, gather_probe, l2_fetch_granularity,
+    records_per_glyph, record_bytes, l2_fetch_granularity,
 )
 from .autograd import query_fn, sh_bake_fn  # noqa: F401

@@ -72,6 +72,9 @@ _SIGS = {
     "shm_query_recon": (C.c_int, [_VP, _I32, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "shm_tune_query": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "shm_tune_reset": (C.c_int, []),
+    "shm_query_binned_workspace_bytes": (C.c_int64, [_VP, _I64, _I64]),
+    "shm_query_binned_bins": (C.c_int32, [_VP, _I64, C.POINTER(C.c_int32)]),
+    "shm_query_binned": (C.c_int, [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _SZ, _VP, _VP]),
     "shm_sh_basis_bytes": (C.c_int64, [_I32, _I32]),
     "shm_sh_basis": (C.c_int, [_I32, _I32, _VP, _VP]),
     "shm_build_lut": (C.c_int, [_VP, _VP, _VP, _SZ, _VP]),
@@ -87,7 +90,6 @@ _SIGS = {
     "shm_raycast_workspace_bytes": (C.c_int64, [_I32, _I32, _I32]),
     "shm_raycast": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "shm_raycast_noalloc": (C.c_int, [_VP, _VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
-    "shm_gather_probe": (C.c_int, [_VP, _I64, _I32, _I64, _VP, _VP, _VP]),
     "shm_l2_fetch_granularity": (C.c_int, [_I32, C.POINTER(C.c_int32)]),
     "shm_status_string": (C.c_char_p, [C.c_int]),
     "shm_version": (C.c_int32, []),
@@ -267,6 +269,48 @@ def query(lut: Lut, dirs: torch.Tensor, glyph: torch.Tensor = None, seg: torch.T
                          _io_ptr(out.get("grad")), _io_ptr(out.get("normal")), _io_ptr(out.get("chart")),
                          _io_ptr(out.get("fij")), _io_ptr(dev_status), _stream(stream))
     _check(st, "shm_query")
+    return out
+
+
+def query_binned_workspace_bytes(lut: Lut, Q: int, band_bytes: int = 0) -> int:
+    """shm_query_binned_workspace_bytes (raises ShmError for an unsupported table)."""
+    n = int(lib().shm_query_binned_workspace_bytes(C.byref(lut.c()), int(Q), int(band_bytes)))
+    if n < 0:
+        raise ShmError("shm_query_binned_workspace_bytes: unsupported table (uniform resolution needed)")
+    return n
+
+
+def query_binned_workspace(lut: Lut, Q: int, band_bytes: int = 0, device="cuda") -> torch.Tensor:
+    """Device workspace for shm_query_binned on Q queries (uint8, 256-byte aligned by the allocator)."""
+    return torch.empty(max(query_binned_workspace_bytes(lut, Q, band_bytes), 1), dtype=torch.uint8, device=device)
+
+
+def query_binned_bins(lut: Lut, band_bytes: int = 0) -> dict:
+    """shm_query_binned_bins: bins (6 faces x bands) and cell rows per band for this table."""
+    rows = C.c_int32(0)
+    B = int(lib().shm_query_binned_bins(C.byref(lut.c()), int(band_bytes), C.byref(rows)))
+    if B < 0:
+        raise ShmError("shm_query_binned_bins: unsupported table")
+    return {"bins": B, "band_rows": rows.value}
+
+
+def query_binned(lut: Lut, dirs: torch.Tensor, ws: torch.Tensor, band_bytes: int = 0,
+                 want=("R", "grad", "normal"), out: dict = None, dev_status: torch.Tensor = None,
+                 stream=None) -> dict:
+    """shm_query_binned: every query on glyph 0 of a uniform-resolution table, partitioned by table
+    region on the device so that the regions in flight stay in L2; outputs (R, grad, normal, chart)
+    in query order, equal to shm_query's.  ws from query_binned_workspace(lut, Q, band_bytes)."""
+    _need(dirs, torch.float32, name="dirs")
+    Q = dirs.shape[0]
+    out = {} if out is None else out
+    shapes = {"R": (Q,), "grad": (Q, 3), "normal": (Q, 3), "chart": (Q, 2)}
+    for k in want:
+        if k not in out:
+            out[k] = _io_empty(shapes[k], torch.float32, dirs)
+    st = lib().shm_query_binned(C.byref(lut.c()), Q, _io_ptr(dirs), _io_ptr(out.get("R")), _io_ptr(out.get("grad")),
+                                _io_ptr(out.get("normal")), _io_ptr(out.get("chart")), int(band_bytes), _ptr(ws),
+                                ws.numel() * ws.element_size(), _io_ptr(dev_status), _stream(stream))
+    _check(st, "shm_query_binned")
     return out
 
 
@@ -534,7 +578,11 @@ def raycast(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm: c_rayc
 
 def raycast_noalloc(lut: Lut, objs: torch.Tensor, n_obj: int, cam: c_camera, prm: c_raycast_params,
                     want=("rgba", "depth", "normal", "obj_id"), out: dict = None, dev_status=None, stream=None) -> dict:
-    """shm_raycast_noalloc: ray casting with the library's static device workspace (no allocation)."""
+    """shm_raycast_noalloc: ray casting with the library's static device workspace, for callers that
+    cannot allocate device memory while they render.  The outputs requested in `want` that are not
+    in `out` are allocated here by torch; pass every buffer in `out` to allocate nothing at all.
+    The static workspace is not exposed, so the surface-query counter that raycast_query_count reads
+    from a caller's shm_raycast workspace cannot be read for this entry point."""
     W, H = cam.W, cam.H
     dev = lut.data.device
     out = {} if out is None else out
@@ -554,22 +602,10 @@ def raycast_query_count(ws: torch.Tensor) -> int:
     return int(ws[8:16].view(torch.int64).item())
 
 
-# ------------------------------------------------------------------------------------------- measurement aid
+# ------------------------------------------------------------------------------------------- L2 hint
 def l2_fetch_granularity(nbytes: int = -1) -> int:
     """shm_l2_fetch_granularity: set the context's L2 fetch granularity hint (0..128 B; -1 only
     reads it).  Returns the value before the call."""
     prev = C.c_int32(-1)
     _check(lib().shm_l2_fetch_granularity(int(nbytes), C.byref(prev)), "shm_l2_fetch_granularity")
     return prev.value
-
-
-def gather_probe(table: torch.Tensor, block_bytes: int, inp: torch.Tensor, out: torch.Tensor = None, stream=None):
-    """shm_gather_probe: the random-gather traffic of a query batch (12 B in, one block gathered,
-    28 B out per item) without the arithmetic."""
-    _need(inp, torch.float32, name="in")
-    Q = inp.shape[0]
-    if out is None:
-        out = torch.empty((Q, 7), dtype=torch.float32, device=inp.device)
-    _check(lib().shm_gather_probe(_ptr(table), table.numel() * table.element_size(), int(block_bytes), Q, _ptr(inp),
-                                  _ptr(out), _stream(stream)), "shm_gather_probe")
-    return out

@@ -269,6 +269,51 @@ shm_status shm_tune_reset(void)
     return SHM_OK;
 }
 
+int64_t shm_query_binned_workspace_bytes(const shm_lut* lut, int64_t Q, int64_t band_bytes)
+{
+    if (check_lut(lut) != SHM_OK || !hermite_layout(lut->layout) || lut->N_uniform <= 0 || Q < 0 || band_bytes < 0)
+        return -1;
+    return binned_workspace_bytes(view(lut), Q, band_bytes);
+}
+
+int32_t shm_query_binned_bins(const shm_lut* lut, int64_t band_bytes, int32_t* band_rows)
+{
+    if (check_lut(lut) != SHM_OK || !hermite_layout(lut->layout) || lut->N_uniform <= 0 || band_bytes < 0) return -1;
+    int rows = 0;
+    const int B = binned_bins(view(lut), band_bytes, &rows);
+    if (band_rows) *band_rows = rows;
+    return B;
+}
+
+shm_status shm_query_binned(const shm_lut* lut, int64_t Q, const float* dirs, float* R, float* grad, float* normal,
+                            float* chart, int64_t band_bytes, void* ws, size_t ws_bytes, int32_t* dev_status,
+                            shm_stream stream)
+{
+    shm_status st = check_lut(lut);
+    if (st != SHM_OK) return st;
+    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
+    if (lut->N_uniform <= 0) return SHM_ERR_UNSUPPORTED;
+    if (Q < 0 || (Q > 0 && !dirs) || band_bytes < 0) return SHM_ERR_INVALID_ARG;
+    const int64_t need = binned_workspace_bytes(view(lut), Q, band_bytes);
+    if (need < 0) return SHM_ERR_INVALID_ARG;
+    if (Q > 0 && (!ws || (int64_t)ws_bytes < need)) return SHM_ERR_WORKSPACE;
+    if (((uintptr_t)ws & 255u) != 0) return SHM_ERR_INVALID_ARG;
+    QueryArgs a;
+    a.L = view(lut);
+    a.Q = Q;
+    a.dirs = dirs;
+    a.glyph = nullptr;
+    a.seg = nullptr;
+    a.R = R;
+    a.grad = grad;
+    a.normal = normal;
+    a.chart = chart;
+    a.fij = nullptr;
+    a.dev_status = dev_status;
+    if ((st = resolve_io(a)) != SHM_OK) return st;
+    return map_cuda(launch_query_binned(a, band_bytes, ws, ws_bytes, (cudaStream_t)stream));
+}
+
 shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const float* dirs, const int32_t* glyph,
                            const int64_t* seg, float* R, float* grad, float* normal, float* chart, int32_t* fij,
                            int32_t* dev_status, shm_stream stream)
@@ -292,16 +337,6 @@ shm_status shm_query_recon(const shm_lut* lut, int32_t method, int64_t Q, const 
     a.dev_status = dev_status;
     if ((st = resolve_io(a)) != SHM_OK) return st;
     return map_cuda(launch_query_recon(a, method, (cudaStream_t)stream));
-}
-
-shm_status shm_gather_probe(const void* table, int64_t table_bytes, int32_t block_bytes, int64_t Q, const float* in,
-                            float* out, shm_stream stream)
-{
-    if (!table || Q < 0 || (Q > 0 && (!in || !out))) return SHM_ERR_INVALID_ARG;
-    if (block_bytes < 16 || block_bytes > 64 || block_bytes % 16 != 0 || ((uintptr_t)table & 15u) != 0 ||
-        table_bytes < block_bytes)
-        return SHM_ERR_INVALID_ARG;
-    return map_cuda(launch_gather_probe(table, table_bytes, block_bytes, Q, in, out, (cudaStream_t)stream));
 }
 
 shm_status shm_l2_fetch_granularity(int32_t bytes, int32_t* previous)

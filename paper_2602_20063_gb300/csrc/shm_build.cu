@@ -1,4 +1,4 @@
-// Bake kernels (arXiv 2602.20063, Algorithm 1 and §3.3 "Derivative computation"):
+// Bake kernels (arXiv 2602.20063, Algorithm 1 and §3.3):
 //
 //   k_sh_basis      per stored texel (gutter included) and SH function Y_k the record
 //                   (Y, Y_u h, Y_v h, Y_uv h^2): Y and its Cartesian gradient / Hessian from the

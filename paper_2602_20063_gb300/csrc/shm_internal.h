@@ -145,8 +145,12 @@ cudaError_t launch_query_shape(const QueryArgs& a, int shape, cudaStream_t s);
 int tuned_query_shape(const QueryArgs& a);
 void set_tuned_query_shape(const QueryArgs& a, int shape);
 void reset_tuned_shapes();
-cudaError_t launch_gather_probe(const void* table, int64_t table_bytes, int block_bytes, int64_t Q, const float* in,
-                                float* out, cudaStream_t s);
+// Binned query of one large table (shm_query_binned.cu): partition by (face, band of cell rows)
+// so that the bands in flight stay in L2, query in partitioned order, restore query order.
+constexpr int64_t BINNED_DEFAULT_BAND_BYTES = 32ll << 20;
+int64_t binned_workspace_bytes(const LutView& L, int64_t Q, int64_t band_bytes);
+int binned_bins(const LutView& L, int64_t band_bytes, int* band_rows);
+cudaError_t launch_query_binned(const QueryArgs& a, int64_t band_bytes, void* ws, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_query_bwd(const BackwardArgs& a, cudaStream_t s);
 cudaError_t launch_adam(float* param, float* grad, float* m, float* v, int64_t n, float lr, float beta1, float beta2,
                         float eps, int step, int zero_grad, cudaStream_t s);

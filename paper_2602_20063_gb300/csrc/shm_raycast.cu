@@ -399,7 +399,8 @@ namespace {
 
 // Device address of g_raycast_scratch for the current device.  In host code the array's name is
 // only a host-side stand-in, so the address is looked up once per device (with that device
-// current) and cached.
+// current) and cached per device index.  A cudaDeviceReset unloads the module and leaves the cached
+// address stale; the header tells callers not to use this entry point after one.
 void* raycast_scratch_address(shm_status* st)
 {
     static std::mutex mu;

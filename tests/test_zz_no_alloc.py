@@ -52,12 +52,21 @@ def _camera(S, W, H, eye):
     return S.make_camera(eye, fwd, right, up, 45.0, W, H)
 
 
-def _noalloc(S, L, lut, objs, n, cam, prm):
-    W, H = cam.W, cam.H
-    out = {"rgba": torch.full((H, W, 4), -7.0, device="cuda"), "depth": torch.full((H, W), -7.0, device="cuda"),
-           "normal": torch.full((H, W, 3), -7.0, device="cuda"),
-           "obj_id": torch.full((H, W), -7, dtype=torch.int32, device="cuda")}
-    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+def _outputs(W, H):
+    return ({"rgba": torch.full((H, W, 4), -7.0, device="cuda"), "depth": torch.full((H, W), -7.0, device="cuda"),
+             "normal": torch.full((H, W, 3), -7.0, device="cuda"),
+             "obj_id": torch.full((H, W), -7, dtype=torch.int32, device="cuda")},
+            torch.zeros(1, dtype=torch.int32, device="cuda"))
+
+
+def _device_memory():
+    """(free device bytes as the driver reports them, bytes held by torch's allocator)."""
+    torch.cuda.synchronize()
+    return torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+
+
+def _noalloc(S, L, lut, objs, n, cam, prm, bufs=None):
+    out, st = bufs if bufs is not None else _outputs(cam.W, cam.H)
     rc = L.shm_raycast_noalloc(C.byref(lut.c()), objs.data_ptr(), n, C.byref(cam), C.byref(prm),
                                out["rgba"].data_ptr(), out["depth"].data_ptr(), out["normal"].data_ptr(),
                                out["obj_id"].data_ptr(), st.data_ptr(),
@@ -78,16 +87,36 @@ def test_noalloc_matches_workspace_entry_point_twice():
     S, L = _shm()
     prm = S.make_raycast_params()
     # two different scenes in a row: the second call starts from the first call's leftover scratch
-    for n, seed, W, H, eye in ((27, 11, 320, 200, (3.0, 4.0, 14.0)), (64, 12, 480, 270, (-5.0, 2.0, 16.0))):
+    for k, (n, seed, W, H, eye) in enumerate(((27, 11, 320, 200, (3.0, 4.0, 14.0)),
+                                              (64, 12, 480, 270, (-5.0, 2.0, 16.0)))):
         lut, objs = _scene(S, n, seed)
         cam = _camera(S, W, H, eye)
         ref = S.raycast(lut, objs, n, cam, prm)
-        rc, out, st = _noalloc(S, L, lut, objs, n, cam, prm)
-        torch.cuda.synchronize()
+        bufs = _outputs(W, H)
+        before = _device_memory()
+        rc, out, st = _noalloc(S, L, lut, objs, n, cam, prm, bufs)
+        after = _device_memory()
         assert rc == 0, rc
         assert st.item() == 0
+        if k == 1:
+            # the first call on the device may have set up the library's static array; from then on
+            # a call allocates nothing, neither through the driver nor through torch's pool
+            assert after == before, (before, after)
         assert (ref["obj_id"] >= 0).float().mean() > 0.05
         _same(out, ref)
+        del ref, bufs, out, st  # released before the next call's "before" reading
+
+
+def test_noalloc_python_wrapper():
+    """The binding's raycast_noalloc gives the same image as shm_raycast with a caller workspace."""
+    S, _ = _shm()
+    prm = S.make_raycast_params()
+    lut, objs = _scene(S, 27, 14)
+    cam = _camera(S, 256, 160, (2.0, -3.0, 13.0))
+    ref = S.raycast(lut, objs, 27, cam, prm)
+    out = S.raycast_noalloc(lut, objs, 27, cam, prm)
+    torch.cuda.synchronize()
+    _same(out, ref)
 
 
 def test_noalloc_full_hd_capacity_and_refusal():
