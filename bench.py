@@ -982,9 +982,9 @@ def planet_leg(args, S, torch):
     t_coh = timeit(lambda: S.query(P.lut, P.dc, out=P.out), 3)
     res = {"workload": P.config["workload"], "random_queries": P.config["random_queries"],
            "l2_fetch_granularity_bytes": 64, "fbm_bake_ms": round(bake, 4),
-           "random_binned": form(t_bin, P.Qr, ("binned", "planet_random_binned")),
+           "random_binned": form(t_bin, P.Qr, ("binned", "query_random")),
            "random_direct": form(t_dir, P.Qr, ("direct", "planet_random_direct")),
-           "coherent_direct": form(t_coh, P.Qc, ("direct", "planet_coherent_direct")),
+           "coherent_direct": form(t_coh, P.Qc, ("direct", "query_coherent")),
            "step_ms": round(bake + t_bin + t_coh, 4),
            "step_queries_per_s": (P.Qr + P.Qc) / ((bake + t_bin + t_coh) * 1e-3),
            "note": "frac at 104 B/query = the paper's per-query bytes (4 corner records + direction + outputs, no "

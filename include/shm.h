@@ -225,7 +225,7 @@ typedef struct {
 } shm_source;
 
 /* Bytes of the SH bake basis for resolution N and degree L (host): K = (L+1)^2, M = 4*6(N+2)^2
- * table scalars per glyph, Kp = K rounded up to a multiple of 32; 4 * (K*M + 2*M*Kp). */
+ * table scalars per glyph, Kp = K rounded up to a multiple of 32; 4 * (K*M + 4*M*Kp). */
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
 
 /* Fills `basis` (device, shm_sh_basis_bytes) with every real SH function's record
@@ -233,8 +233,9 @@ int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
  * derivatives converted to the chart by the chain rule (§3.3, Algorithm 1).  The bake of
  * coefficients c is then lut = sum_k c_k basis_k.  Layout (float32): full [K][M] (row k =
  * basis_k's table, texel-major, channel innermost), then hi [M][Kp] and lo [M][Kp] with
- * hi = tf32(full^T), lo = tf32(full^T - hi), zero for k >= K (operands of the tensor-core bake).
- * Compute once per (N, L) and reuse. */
+ * hi = tf32(full^T), lo = tf32(full^T - hi), zero for k >= K (operands of the tensor-core bake),
+ * then hiT [Kp][M] and loT [Kp][M], the same split untransposed (rows k >= K zero; operands of the
+ * tensor-core adjoint of shm_build_lut_backward).  Compute once per (N, L) and reuse. */
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream);
 
 /* Workspace bytes that select the tensor-core engine of shm_build_lut for (lut, src): for SH
@@ -275,8 +276,9 @@ shm_status shm_build_mip(const shm_lut* fine, const shm_lut* coarse, int32_t* de
 
 /* ---------------------------------------------------------------- adjoint (not in the paper) */
 
-/* Flags of shm_query_backward. */
+/* Flags of shm_query_backward and shm_build_lut_backward. */
 #define SHM_BWD_DETERMINISTIC 1u /* fixed summation order: dlut bit-identical from run to run */
+#define SHM_BWD_CUDA_CORES 2u    /* shm_build_lut_backward: the float32 CUDA-core contraction */
 
 /* Reverse mode of shm_query.  Upstream gradients gR [Q], ggrad [Q][3], gnormal [Q][3] (each
  * may be NULL = 0).  Accumulates (+=) dL/d(stored record) into dlut, a float32 TEXEL-layout
@@ -293,11 +295,18 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
                               const float* ggrad, const float* gnormal, const shm_lut* dlut,
                               float* ddirs, uint32_t flags, int32_t* dev_status, shm_stream stream);
 
-/* Reverse mode of the SH bake: dcoeffs[g][k] (=) sum over texels and channels of
- * dlut[g] * basis_k.  dlut: float32 texel layout, uniform N; basis from shm_sh_basis(N, L).
- * flags = 0: the sum over texels is split across CTAs and combined with atomics when there are
- * few (glyph, k) tiles; SHM_BWD_DETERMINISTIC: one thread sums each dcoeffs entry in a fixed order
- * (bit-identical from run to run; slower for a handful of glyphs). */
+/* Reverse mode of the SH bake (Algorithm 1 is linear in the coefficients): dcoeffs[g][k] (=) sum
+ * over texels and channels of dlut[g] * basis_k.  dlut: float32 texel layout, uniform N, 16-byte
+ * aligned; basis from shm_sh_basis(N, L).
+ * Default engine: the tensor cores (tcgen05, kind::tf32 with the 3xTF32 split of both operands,
+ * float32-grade accuracy): CTAs of a thread-block cluster split the texel sum and add their partial
+ * sums in a fixed rank order through distributed shared memory, so the result is bit-identical from
+ * run to run with or without SHM_BWD_DETERMINISTIC.  It applies for K up to 512 and table sizes
+ * whose partial sums fit in shared memory (all L <= 16 at the resolutions used here); otherwise, or
+ * with SHM_BWD_CUDA_CORES, the float32 CUDA-core contraction runs: flags = 0 splits the sum over
+ * texels across CTAs and combines with atomics when there are few (glyph, k) tiles;
+ * SHM_BWD_DETERMINISTIC makes one thread sum each entry in a fixed order.  A bounded wait of the
+ * tensor-core kernel that expires (1 s) leaves dcoeffs unspecified (no status word here). */
 shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* basis,
                                   float* dcoeffs, uint32_t flags, shm_stream stream);
 

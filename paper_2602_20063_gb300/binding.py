@@ -22,6 +22,7 @@ SHM_RECON_NEAREST, SHM_RECON_BILINEAR, SHM_RECON_BICUBIC, SHM_RECON_FAST_BICUBIC
 SHM_SRC_SH, SHM_SRC_SAMPLES, SHM_SRC_BUMPS, SHM_SRC_FBM = 0, 1, 2, 3
 SHM_DEV_NONFINITE, SHM_DEV_BOUNDS, SHM_DEV_TIMEOUT = 1, 2, 4
 SHM_BWD_DETERMINISTIC = 1
+SHM_BWD_CUDA_CORES = 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error", 5: "timeout"}
 
 DTYPES = {SHM_F32: torch.float32, SHM_F16: torch.float16, SHM_BF16: torch.bfloat16}
@@ -471,12 +472,14 @@ def query_backward(lut: Lut, dirs: torch.Tensor, dlut: Lut, gR=None, ggrad=None,
     return ddirs
 
 
-def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None, deterministic=False) -> torch.Tensor:
+def build_lut_backward(dlut: Lut, L: int, basis: torch.Tensor, stream=None, deterministic=False,
+                       cuda_cores=False, out: torch.Tensor = None) -> torch.Tensor:
+    """shm_build_lut_backward: dcoeffs [G][(L+1)^2] from dL/dtable (tensor cores unless cuda_cores)."""
     K = (L + 1) ** 2
-    dc = torch.empty((dlut.n_glyphs, K), dtype=torch.float32, device=dlut.data.device)
-    _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc),
-                                        C.c_uint32(SHM_BWD_DETERMINISTIC if deterministic else 0), _stream(stream)),
-           "shm_build_lut_backward")
+    dc = torch.empty((dlut.n_glyphs, K), dtype=torch.float32, device=dlut.data.device) if out is None else out
+    flags = (SHM_BWD_DETERMINISTIC if deterministic else 0) | (SHM_BWD_CUDA_CORES if cuda_cores else 0)
+    _check(lib().shm_build_lut_backward(C.byref(dlut.c()), L, _ptr(basis), _ptr(dc), C.c_uint32(flags),
+                                        _stream(stream)), "shm_build_lut_backward")
     return dc
 
 

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libshm.so")
-SOURCES = ["shm_api.cu", "shm_query.cu", "shm_query_bwd.cu", "shm_build.cu", "shm_bake_tc.cu", "shm_raycast.cu", "shm_mip.cu", "shm_recon.cu", "shm_query_staged.cu", "shm_query_bwd_det.cu", "shm_query_binned.cu"]
-HEADERS = ["shm_device.cuh", "shm_internal.h", "shm_query_kernel.cuh", "shm_stage.cuh", "shm_bwd.cuh"]
+SOURCES = ["shm_api.cu", "shm_query.cu", "shm_query_bwd.cu", "shm_build.cu", "shm_bake_tc.cu", "shm_raycast.cu", "shm_mip.cu", "shm_recon.cu", "shm_query_staged.cu", "shm_query_bwd_det.cu", "shm_query_binned.cu", "shm_bake_tc_bwd.cu"]
+HEADERS = ["shm_tc.cuh", "shm_device.cuh", "shm_internal.h", "shm_query_kernel.cuh", "shm_stage.cuh", "shm_bwd.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -357,7 +357,7 @@ int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
 {
     if (N < 1 || L < 0 || L > 20) return -1;
     const int64_t K = (int64_t)(L + 1) * (L + 1), M = 4LL * 6 * (N + 2) * (N + 2);
-    return (K * M + 2 * M * sh_kpad(L)) * (int64_t)sizeof(float);
+    return (K * M + 4 * M * sh_kpad(L)) * (int64_t)sizeof(float);
 }
 
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream)
@@ -365,7 +365,9 @@ shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream)
     if (N < 1 || N > (1 << 14) || L < 0 || L > 20 || !basis) return SHM_ERR_INVALID_ARG;
     cudaError_t e = launch_sh_basis(N, L, basis, (cudaStream_t)stream);
     if (e != cudaSuccess) return SHM_ERR_CUDA;
-    return map_cuda(launch_basis_split(N, L, basis, (cudaStream_t)stream));
+    e = launch_basis_split(N, L, basis, (cudaStream_t)stream);
+    if (e != cudaSuccess) return SHM_ERR_CUDA;
+    return map_cuda(launch_basis_split_t(N, L, basis, (cudaStream_t)stream));
 }
 
 int64_t shm_build_workspace_bytes(const shm_lut* lut, const shm_source* src)
@@ -552,7 +554,14 @@ shm_status shm_build_lut_backward(const shm_lut* dlut, int32_t L, const float* b
     if (dlut->dtype != SHM_F32 || dlut->layout != SHM_LAYOUT_TEXEL || dlut->N_uniform <= 0)
         return SHM_ERR_UNSUPPORTED;
     if (L < 0 || L > 20 || !basis || !dcoeffs) return SHM_ERR_INVALID_ARG;
-    if ((flags & ~(uint32_t)SHM_BWD_DETERMINISTIC) != 0) return SHM_ERR_INVALID_ARG;
+    if ((flags & ~(uint32_t)(SHM_BWD_DETERMINISTIC | SHM_BWD_CUDA_CORES)) != 0) return SHM_ERR_INVALID_ARG;
+    if (((uintptr_t)dlut->data & 15u) != 0 || ((uintptr_t)basis & 15u) != 0) return SHM_ERR_INVALID_ARG;
+    if (!(flags & SHM_BWD_CUDA_CORES)) {
+        const cudaError_t e = launch_sh_build_bwd_tc(dlut->N_uniform, dlut->n_glyphs, L, (const float*)dlut->data,
+                                                     basis, dcoeffs, nullptr, (cudaStream_t)stream);
+        if (e != cudaErrorNotSupported) return map_cuda(e);
+        (void)cudaGetLastError();
+    }
     return map_cuda(launch_sh_build_bwd(dlut->N_uniform, dlut->n_glyphs, L, (const float*)dlut->data, basis, dcoeffs,
                                         (flags & SHM_BWD_DETERMINISTIC) != 0, (cudaStream_t)stream));
 }

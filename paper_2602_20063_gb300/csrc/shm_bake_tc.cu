@@ -28,19 +28,13 @@
 // tensor pipe idle 70 % of the time.  Other dtypes / layouts keep per-thread stores.
 // Every mbarrier wait is bounded (1 s); on expiry the CTA raises SHM_DEV_TIMEOUT, drains its own
 // copies and MMAs with bounded waits, frees TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include <mutex>
-
-#include "shm_internal.h"
+#include "shm_tc.cuh"
 
 namespace shm {
 namespace tc {
 
 constexpr int TM = 128;  // table columns per tile (MMA M)
 constexpr int TN = 256;  // glyphs per tile (MMA N)
-constexpr int KC = 16;   // K per stage: 16 x 4 B = one 64-byte swizzle row
 constexpr int NSTAGE = 3;
 constexpr uint32_t A_BYTES = TM * KC * 4;
 constexpr uint32_t B_BYTES = TN * KC * 4;
@@ -50,10 +44,6 @@ constexpr uint32_t OUT_BYTES = OG * TM * 4;           // one [32 glyphs][128 col
 constexpr uint32_t BAR_BYTES = 256;
 constexpr int NOUT = 4;                               // output boxes in flight per CTA
 constexpr uint32_t SMEM_BYTES = NSTAGE * STAGE_BYTES + NOUT * OUT_BYTES + BAR_BYTES + 1024;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;   // 1 s
-constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;   // 100 ms
-
 // kind::tf32 instruction descriptor: D f32, A and B tf32, both K-major, N = 256, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
@@ -68,78 +58,8 @@ struct Args {
     int32_t* dev_status;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t globaltimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for the phase with the given parity to complete.  Returns false after `limit` ns or as
-// soon as another role has raised the abort flag.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (globaltimer() - t0 > limit) {
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y)
-{
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];"
-                 ::"l"((uint64_t)map), "r"(x), "r"(y), "r"(src)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // at most NOUT - 1 stores may still be reading their shared boxes
 __device__ __forceinline__ void bulk_wait_read_free() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(NOUT - 1) : "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // AND of `ok` over the 128 epilogue threads (named barrier 1): all leave or all stay.
@@ -157,9 +77,6 @@ __device__ __forceinline__ bool epi_all(bool ok)
     return r != 0;
 }
 
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc)
 {
     asm volatile(
@@ -168,37 +85,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
         ::"r"(d), "l"(a), "l"(b), "r"(IDESC), "r"(acc)
         : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row atoms of 512 B (SBO).
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((8u * KC * 4u) >> 4) << 32;  // stride byte offset between 8-row groups
-    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
-    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
-    return d;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(256, 1)
@@ -386,14 +272,6 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-// tf32 round-to-nearest (ties away) of a float: the tensor cores read the top 19 bits.
-__device__ __forceinline__ float tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // rows x K float32 (row stride ld_in) -> hi, lo [rows][Kp] (zero padded)
 __global__ void k_split_rows(const float* __restrict__ in, int rows, int K, int64_t ld_in, int64_t col_stride,
                              int Kp, float* __restrict__ hi, float* __restrict__ lo)
@@ -407,22 +285,6 @@ __global__ void k_split_rows(const float* __restrict__ in, int rows, int K, int6
         hi[e] = h;
         lo[e] = tf32_rna(v - h);
     }
-}
-
-using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
-
-static EncodeFn encode_fn()
-{
-    static EncodeFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeFn>(p);
-    });
-    return fn;
 }
 
 static bool make_map(CUtensorMap* m, const float* base, int rows, int Kp, int box_rows)
@@ -452,6 +314,7 @@ static bool make_out_map(CUtensorMap* m, float* base, int G, int M)
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
 
 }  // namespace tc
 
@@ -513,5 +376,6 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     tc::k_sh_gemm_tc<<<grid, 256, tc::SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, mOut, a);
     return cudaGetLastError();
 }
+
 
 }  // namespace shm

@@ -1,0 +1,387 @@
+// Tensor-core adjoint of the SH bake (sm_103a): see the comment at the top of namespace bwd.
+#include "shm_tc.cuh"
+
+namespace shm {
+namespace tc {
+// ------------------------------------------------------------------------------------------
+// Adjoint of the bake on the tensor cores.  The bake is linear in the coefficients (Algorithm 1:
+// table = sum_k c_k basis_k), so its reverse mode is the transposed contraction
+//     dcoeffs[g][k] = sum_c dlut[g][c] basis[k][c]                     (c over the 4T table scalars)
+// with glyphs on the MMA M side (128 per TMEM accumulator, up to four accumulators per CTA) and the
+// coefficients on N (K padded to Kp, one MMA of N = Kp, or two of Kp / 2 above 256).  Operands:
+//   A = dlut tiles [128 glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
+//       the four converter warps into tf32 hi (overwriting the raw tile) and lo = tf32(x - hi);
+//   B = the transposed tf32 split of the basis, hiT / loT [Kp][4T] (part of shm_sh_basis's buffer).
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, as the forward bake).
+// The c range is split over the S CTAs of a thread-block cluster; at the end every CTA writes its
+// partial accumulators to shared memory and each CTA sums a slice of them over the cluster's ranks
+// in rank order through distributed shared memory, so the result does not depend on timing
+// (deterministic, no atomics, no workspace).
+//   warp 0 lane 0: TMA producer     warp 1: TMEM allocation, lane 0 issues the MMAs
+//   warps 4-7: tf32 split of each stage, then the epilogue (TMEM -> shared partials)
+// Every mbarrier wait is bounded (1 s) and raises SHM_DEV_TIMEOUT on expiry; the cluster barriers
+// are reached by every thread of every CTA the same number of times, aborted or not.
+namespace bwd {
+
+constexpr int MG = 128;                       // glyph rows per accumulator (MMA M)
+constexpr uint32_t A_TILE = MG * KC * 4;      // 8 KB
+constexpr int MAX_ACC = 4;
+constexpr uint32_t STAGE_CAP = 196 * 1024;    // shared memory for the stages (and the partials after them)
+constexpr uint32_t BAR_BYTES = 1024;
+
+struct Args {
+    int M4;        // table scalars per glyph (4T), the reduction length
+    int G, K, Kp;
+    int NB;        // N of one MMA
+    int nblk;      // MMAs per accumulator and K step (Kp = nblk NB)
+    int tgc;       // accumulators (glyph sub-tiles of 128) per CTA
+    int S;         // CTAs per cluster (splits of the c range)
+    int NC;        // stages over the whole c range
+    int nstage;    // pipeline depth
+    uint32_t a_bytes, b_bytes, stage_bytes;
+    float* dcoeffs;
+    int32_t* dev_status;
+};
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float ld_dsmem(uint32_t local_addr, uint32_t rank)
+{
+    uint32_t remote;
+    float v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local_addr), "r"(rank));
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t idesc(int NB)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(MG >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32_n(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1)
+    k_sh_gemm_bwd_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBh,
+                     const __grid_constant__ CUtensorMap mBl, Args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* bars = smem;
+    uint8_t* stages = smem + BAR_BYTES;
+    const uint32_t full0 = smem_u32(bars), conv0 = full0 + 8 * 8, empty0 = conv0 + 8 * 8, tfull = empty0 + 8 * 8,
+                   drain = tfull + 8;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 512);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 520);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int group = blockIdx.x / a.S;
+    const int g_base = group * a.tgc * MG;
+    const int c0 = (int)(((int64_t)a.NC * rank) / a.S), c1 = (int)(((int64_t)a.NC * (rank + 1)) / a.S);
+    const int nst = c1 - c0;
+    const uint32_t ID = idesc(a.NB);
+
+    auto stA = [&](int st) { return stages + (size_t)st * a.stage_bytes; };
+    auto stAlo = [&](int st) { return stages + (size_t)st * a.stage_bytes + a.a_bytes; };
+    auto stBh = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * a.a_bytes; };
+    auto stBl = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * a.a_bytes + a.b_bytes; };
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < a.nstage; ++st) {
+            mbar_init(full0 + 8 * st, 1);
+            mbar_init(conv0 + 8 * st, 128);
+            mbar_init(empty0 + 8 * st, 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        int it = 0;
+        for (; it < nst; ++it) {
+            const int st = it % a.nstage;
+            const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
+            if (!mbar_wait(empty0 + 8 * st, ph ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
+            const uint32_t fb = full0 + 8 * st;
+            const int c = (c0 + it) * KC;
+            mbar_expect_tx(fb, a.a_bytes + 2 * a.b_bytes);
+            for (int q = 0; q < a.tgc; ++q) tma_load_2d(smem_u32(stA(st) + q * A_TILE), &mA, c, g_base + q * MG, fb);
+            for (int b = 0; b < a.nblk; ++b) {
+                tma_load_2d(smem_u32(stBh(st) + b * a.NB * KC * 4), &mBh, c, b * a.NB, fb);
+                tma_load_2d(smem_u32(stBl(st) + b * a.NB * KC * 4), &mBl, c, b * a.NB, fb);
+            }
+        }
+        if (it < nst) {
+            // aborted: the last load issued into each stage must land before the shared memory is reused
+            for (int k = 1; k <= a.nstage && k <= it; ++k) {
+                const int last = it - k;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(full0 + 8 * (last % a.nstage), (uint32_t)(last / a.nstage) & 1) &&
+                       globaltimer() - t0 < DRAIN_LIMIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        bool ok = true, any = false;
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % a.nstage;
+            const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
+            if (!mbar_wait(conv0 + 8 * st, ph, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+            fence_after();
+            for (int q = 0; q < a.tgc; ++q) {
+                const uint32_t ah = smem_u32(stA(st) + q * A_TILE), al = smem_u32(stAlo(st) + q * A_TILE);
+                for (int b = 0; b < a.nblk; ++b) {
+                    const uint32_t d = tmem + (uint32_t)(q * a.Kp + b * a.NB);
+                    const uint32_t bh = smem_u32(stBh(st) + b * a.NB * KC * 4), bl = smem_u32(stBl(st) + b * a.NB * KC * 4);
+#pragma unroll
+                    for (int kk = 0; kk < KC / 8; ++kk) {
+                        const uint32_t o = kk * 32;
+                        mma_tf32_n(d, sdesc(ah + o), sdesc(bh + o), ID, (it | kk) != 0);
+                        mma_tf32_n(d, sdesc(ah + o), sdesc(bl + o), ID, 1);
+                        mma_tf32_n(d, sdesc(al + o), sdesc(bh + o), ID, 1);
+                    }
+                }
+            }
+            any = true;
+            mma_commit(empty0 + 8 * st);
+        }
+        if (ok) {
+            mma_commit(tfull);
+        } else if (any) {
+            mma_commit(drain);
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
+            }
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- tf32 split of each stage
+        const int t = threadIdx.x - 128;
+        const int n4 = (int)(a.a_bytes / 16);
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % a.nstage;
+            const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
+            if (!mbar_wait(full0 + 8 * st, ph, abort_flag, WAIT_LIMIT_NS)) break;
+            float4* hi = reinterpret_cast<float4*>(stA(st));
+            float4* lo = reinterpret_cast<float4*>(stAlo(st));
+            for (int i = t; i < n4; i += 128) {
+                const float4 x = hi[i];
+                float4 h, l;
+                h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
+                l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
+                hi[i] = h;
+                lo[i] = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(conv0 + 8 * st);
+        }
+    }
+    __syncthreads();
+    // ---------------------------------------------------------------- epilogue: cluster reduction
+    if (warp >= 4 && !*abort_flag) {
+        if (!mbar_wait(tfull, 0, abort_flag, WAIT_LIMIT_NS)) *abort_flag = 1;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const bool aborted = *abort_flag != 0;
+    float* P = reinterpret_cast<float*>(stages);  // [128][Kp + 1] partials of one accumulator
+    const int PS = a.Kp + 1;
+    const uint32_t P_s = smem_u32(P);
+    const int E = MG * a.K;
+    const int e0 = (int)(((int64_t)E * rank) / a.S), e1 = (int)(((int64_t)E * (rank + 1)) / a.S);
+    for (int q = 0; q < a.tgc; ++q) {
+        if (warp >= 4 && !aborted) {
+            const int wq = warp & 3, row = 32 * wq + lane;
+            for (int cc = 0; cc < a.Kp; cc += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(q * a.Kp + cc), r);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) P[row * PS + cc + i] = __uint_as_float(r[i]);
+            }
+        }
+        cluster_sync();
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int row = e / a.K, k = e - row * a.K;
+            const int g = g_base + q * MG + row;
+            float sum = 0.0f;
+            for (int rr = 0; rr < a.S; ++rr) sum += ld_dsmem(P_s + 4u * (uint32_t)(row * PS + k), (uint32_t)rr);
+            if (g < a.G && !aborted) a.dcoeffs[(int64_t)g * a.K + k] = sum;
+        }
+        cluster_sync();
+    }
+    if (threadIdx.x == 0 && aborted && a.dev_status) atomicOr(a.dev_status, SHM_DEV_TIMEOUT);
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// c (Kp x M4) transposed tf32 split of the basis: hiT[k][c] = tf32(full[k][c]), loT = tf32(full - hi),
+// rows k >= K zero.
+__global__ void k_split_basis_t(const float* __restrict__ full, int K, int Kp, int64_t M4, float* __restrict__ hiT,
+                                float* __restrict__ loT)
+{
+    const int64_t n = (int64_t)Kp * M4;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / M4;
+        const float v = (k < K) ? __ldg(full + e) : 0.0f;
+        const float h = tf32_rna(v);
+        hiT[e] = h;
+        loT[e] = tf32_rna(v - h);
+    }
+}
+
+// 2-D map over a row-major [rows][M4] f32 array, boxes of [box_rows][16 c], 64-byte swizzle.
+static bool make_map_c(CUtensorMap* m, const float* base, int rows, int M4, int box_rows)
+{
+    EncodeFn enc = encode_fn();
+    if (!enc || ((uintptr_t)base & 15u) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)M4, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)M4 * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Plan of the tensor-core adjoint for (G, K, Kp, M4) on `sms` SMs; false when it does not apply
+// (the CUDA-core kernel is used then).
+static bool plan(int G, int K, int Kp, int M4, int sms, int max_cluster, Args* out)
+{
+    Args a{};
+    a.M4 = M4; a.G = G; a.K = K; a.Kp = Kp;
+    if (Kp > 512) return false;
+    a.nblk = Kp > 256 ? 2 : 1;
+    a.NB = Kp / a.nblk;
+    if (a.NB % 16 != 0 || a.NB > 256) return false;
+    a.tgc = 512 / Kp;
+    if (a.tgc > MAX_ACC) a.tgc = MAX_ACC;
+    if (a.tgc < 1) return false;
+    // fewer glyphs per CTA while even the largest clusters could not fill the SMs
+    while (a.tgc > 1 && (int64_t)((G + a.tgc * MG - 1) / (a.tgc * MG)) * max_cluster < sms) --a.tgc;
+    const int groups = (G + a.tgc * MG - 1) / (a.tgc * MG);
+    a.S = sms / groups;
+    if (a.S > max_cluster) a.S = max_cluster;
+    if (a.S < 1) a.S = 1;
+    a.NC = (M4 + KC - 1) / KC;
+    if (a.S > a.NC) a.S = a.NC;
+    a.a_bytes = (uint32_t)a.tgc * A_TILE;
+    a.b_bytes = (uint32_t)Kp * KC * 4;
+    a.stage_bytes = 2 * a.a_bytes + 2 * a.b_bytes;
+    a.nstage = (int)(STAGE_CAP / a.stage_bytes);
+    if (a.nstage > 8) a.nstage = 8;
+    if (a.nstage < 2) return false;
+    if ((uint64_t)MG * (Kp + 1) * 4 > (uint64_t)a.nstage * a.stage_bytes) return false;  // partials fit
+    *out = a;
+    return true;
+}
+
+}  // namespace bwd
+}  // namespace tc
+
+// basis: [K][M] full, hi [M][Kp], lo [M][Kp], then the adjoint's hiT [Kp][M] and loT [Kp][M]
+cudaError_t launch_basis_split_t(int N, int L, float* basis, cudaStream_t s)
+{
+    const int K = (L + 1) * (L + 1), Kp = sh_kpad(L);
+    const int64_t M = 4LL * 6 * (N + 2) * (N + 2);
+    float* hiT = basis + (int64_t)K * M + 2 * M * Kp;
+    float* loT = hiT + (int64_t)Kp * M;
+    const int64_t n = (int64_t)Kp * M;
+    tc::bwd::k_split_basis_t<<<(unsigned)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8), 256, 0, s>>>(
+        basis, K, Kp, M, hiT, loT);
+    return cudaGetLastError();
+}
+
+// Tensor-core adjoint of the SH bake; returns cudaErrorNotSupported when its plan does not apply
+// (the caller then runs the CUDA-core kernel).
+cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
+                                   int32_t* dev_status, cudaStream_t s)
+{
+    using namespace tc::bwd;
+    const int K = (L + 1) * (L + 1), Kp = sh_kpad(L);
+    const int M4 = 4 * 6 * (N + 2) * (N + 2);
+    const float* hiT = basis + (int64_t)K * M4 + 2LL * M4 * Kp;
+    const float* loT = hiT + (int64_t)Kp * M4;
+    cudaError_t e = ensure_dynamic_smem((const void*)k_sh_gemm_bwd_tc, (int)(1024 + BAR_BYTES + STAGE_CAP));
+    if (e != cudaSuccess) return e;
+    // clusters of up to 16 CTAs where the device allows them, else the portable 8
+    static int max_cluster = 0;
+    if (max_cluster == 0) {
+        max_cluster = 8;
+        if (cudaFuncSetAttribute((const void*)k_sh_gemm_bwd_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(16, 1, 1);
+            q.blockDim = dim3(256, 1, 1);
+            q.dynamicSmemBytes = 1024 + BAR_BYTES + STAGE_CAP;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = 16;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            q.attrs = &at;
+            q.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_sh_gemm_bwd_tc, &q) == cudaSuccess && n > 0)
+                max_cluster = 16;
+        }
+        (void)cudaGetLastError();
+    }
+    Args a;
+    if (!plan(G, K, Kp, M4, sm_count(), max_cluster, &a)) return cudaErrorNotSupported;
+    CUtensorMap mA, mBh, mBl;
+    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, a.NB) || !make_map_c(&mBl, loT, Kp, M4, a.NB))
+        return cudaErrorNotSupported;
+    a.dcoeffs = dcoeffs;
+    a.dev_status = dev_status;
+    const int groups = (G + a.tgc * MG - 1) / (a.tgc * MG);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(groups * a.S), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 1024 + BAR_BYTES + (size_t)a.nstage * a.stage_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)a.S;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sh_gemm_bwd_tc, mA, mBh, mBl, a);
+}
+}  // namespace shm

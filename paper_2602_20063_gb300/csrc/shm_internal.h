@@ -165,6 +165,9 @@ cudaError_t launch_sh_build(const LutView& out, void* data, int L, const float* 
                             cudaStream_t s);
 cudaError_t launch_sh_build_bwd(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs, bool det,
                                 cudaStream_t s);
+cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const float* basis, float* dcoeffs,
+                                   int32_t* dev_status, cudaStream_t s);
+cudaError_t launch_basis_split_t(int N, int L, float* basis, cudaStream_t s);
 cudaError_t launch_sh_value(const LutView& out, void* data, int L, const float* coeffs, cudaStream_t s);
 cudaError_t launch_query_recon(const QueryArgs& a, int method, cudaStream_t s);
 cudaError_t launch_fd_build(const LutView& out, void* data, const shm_source& src, const Sizes& sz, cudaStream_t s);

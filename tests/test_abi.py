@@ -45,7 +45,8 @@ def test_host_helpers(lib):
     assert lib.shm_records_per_glyph(0, 0) == -1
     assert lib.shm_record_bytes(0, 0) == 16 and lib.shm_record_bytes(2, 0) == 8 and lib.shm_record_bytes(0, 1) == 64
     M = 4 * 6 * 34 * 34
-    assert lib.shm_sh_basis_bytes(32, 8) == (81 * M + 2 * M * 96) * 4  # full [K][M] + tf32 hi/lo [M][Kp]
+    # full [K][M] + tf32 hi/lo [M][Kp] (bake operands) + hiT/loT [Kp][M] (adjoint operands)
+    assert lib.shm_sh_basis_bytes(32, 8) == (81 * M + 4 * M * 96) * 4
     assert lib.shm_sh_basis_bytes(32, 21) == -1
     Ns = (C.c_int32 * 3)(16, 32, 5)
     offs = (C.c_int64 * 3)()

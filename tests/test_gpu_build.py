@@ -35,8 +35,16 @@ def _split_basis(buf, N, L):
     Kp = (K + 31) // 32 * 32
     full = buf[:K * M].reshape(K, M)
     hi = buf[K * M:K * M + M * Kp].reshape(M, Kp)
-    lo = buf[K * M + M * Kp:].reshape(M, Kp)
+    lo = buf[K * M + M * Kp:K * M + 2 * M * Kp].reshape(M, Kp)
     return full, hi, lo, K, Kp
+
+
+def _split_basis_t(buf, N, L):
+    """The adjoint's operands after the forward ones: hiT, loT [Kp][M]."""
+    K, M = (L + 1) ** 2, 4 * 6 * (N + 2) ** 2
+    Kp = (K + 31) // 32 * 32
+    o = K * M + 2 * M * Kp
+    return buf[o:o + Kp * M].reshape(Kp, M), buf[o + Kp * M:o + 2 * Kp * M].reshape(Kp, M)
 
 
 @pytest.mark.parametrize("N,L", [(10, 4), (32, 8), (7, 16)])
@@ -54,6 +62,11 @@ def test_sh_basis(S, N, L):
     assert np.all(hi[:, K:] == 0) and np.all(lo[:, K:] == 0)
     fT = full.T.astype(np.float64)
     assert np.all(np.abs(hi[:, :K] + lo[:, :K].astype(np.float64) - fT) <= 2.0 ** -21 * np.abs(fT))
+    # the adjoint's untransposed split: the same values row by row, zero rows k >= K
+    hiT, loT = _split_basis_t(buf, N, L)
+    assert buf.size == K * full.shape[1] + 4 * full.shape[1] * Kp
+    assert np.array_equal(hiT[:K], hi[:, :K].T) and np.array_equal(loT[:K], lo[:, :K].T)
+    assert np.all(hiT[K:] == 0) and np.all(loT[K:] == 0)
 
 
 @pytest.mark.parametrize("engine", ["simt", "tcgen05"])
