@@ -391,8 +391,22 @@ class GlyphField:
                                               want_ddirs=True), n)
         bwd_det = timeit(lambda: S.query_backward(self.lut, self.dirs, dl, gR=gR, ggrad=gG, gnormal=gN, seg=self.seg,
                                                   want_ddirs=True, deterministic=True), n)
+        # the bake's adjoint (dL/dcoeffs from dL/dtable): tensor cores vs the float32 CUDA-core contraction
+        dco = torch.empty((self.G, (self.L + 1) ** 2), dtype=torch.float32, device="cuda")
+        bake_bwd = timeit(lambda: S.build_lut_backward(dl, self.L, self.basis, out=dco), n)
+        bake_bwd_simt = timeit(lambda: S.build_lut_backward(dl, self.L, self.basis, out=dco, cuda_cores=True), n)
+        dl_bytes = dl.data.numel() * 4
+        ex["bake_bwd"] = {"ms": round(bake_bwd, 4), "cuda_cores_ms": round(bake_bwd_simt, 4),
+                          "speedup_vs_cuda_cores": round(bake_bwd_simt / bake_bwd, 3),
+                          "achieved_GBps": round(dl_bytes / (bake_bwd * 1e-3) / 1e9, 1),
+                          "frac_of_measured_hbm": round(dl_bytes / (bake_bwd * 1e-3) / 1e9 / load_peaks()["hbm_gbs"], 3),
+                          "per_unit": f"{dl_bytes / self.G:.0f} B of dL/dtable read per glyph (the basis operands, "
+                                      "21 MB, come from L2); 3 x 2 x Kp x 4T tf32 flop per glyph on the tensor cores",
+                          "note": "dcoeffs = dL/dtable . basis^T, tcgen05 3xTF32 with a fixed-order cluster reduction "
+                                  "(deterministic); cuda_cores: the float32 SIMT contraction with split-K atomics"}
+        del dco
         ex["fwd_bwd"] = {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4), "fwd_plus_bwd_over_fwd": round((fwd + bwd) / fwd, 3),
-                         "bwd_deterministic_ms": round(bwd_det, 4),
+                         "bwd_deterministic_ms": round(bwd_det, 4), "bake_bwd_ms": round(bake_bwd, 4),
                          "note": "backward = recompute + 4 float4 atomics per query into a float32 texel table + d/ddirs; "
                                  "deterministic = per-glyph CTA, chunks sorted by cell, per-cell sums added in a fixed order"}
         ref = {k: v.clone() for k, v in self.out.items()}

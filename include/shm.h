@@ -299,11 +299,11 @@ shm_status shm_query_backward(const shm_lut* lut, int64_t Q, const float* dirs,
  * over texels and channels of dlut[g] * basis_k.  dlut: float32 texel layout, uniform N, 16-byte
  * aligned; basis from shm_sh_basis(N, L).
  * Default engine: the tensor cores (tcgen05, kind::tf32 with the 3xTF32 split of both operands,
- * float32-grade accuracy): CTAs of a thread-block cluster split the texel sum and add their partial
- * sums in a fixed rank order through distributed shared memory, so the result is bit-identical from
- * run to run with or without SHM_BWD_DETERMINISTIC.  It applies for K up to 512 and table sizes
- * whose partial sums fit in shared memory (all L <= 16 at the resolutions used here); otherwise, or
- * with SHM_BWD_CUDA_CORES, the float32 CUDA-core contraction runs: flags = 0 splits the sum over
+ * the MMA sums drained into float32 registers every 256 texel scalars, float32-grade accuracy); for
+ * few glyphs the CTAs of a thread-block cluster split the texel sum and add their partial sums in a
+ * fixed rank order through distributed shared memory, so the result is bit-identical from run to
+ * run with or without SHM_BWD_DETERMINISTIC.  It applies for K padded to 32 up to 128 (L <= 10);
+ * otherwise, or with SHM_BWD_CUDA_CORES, the float32 CUDA-core contraction runs: flags = 0 splits the sum over
  * texels across CTAs and combines with atomics when there are few (glyph, k) tiles;
  * SHM_BWD_DETERMINISTIC makes one thread sum each entry in a fixed order.  A bounded wait of the
  * tensor-core kernel that expires (1 s) leaves dcoeffs unspecified (no status word here). */

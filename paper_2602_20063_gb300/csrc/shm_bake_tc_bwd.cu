@@ -7,38 +7,44 @@ namespace tc {
 // Adjoint of the bake on the tensor cores.  The bake is linear in the coefficients (Algorithm 1:
 // table = sum_k c_k basis_k), so its reverse mode is the transposed contraction
 //     dcoeffs[g][k] = sum_c dlut[g][c] basis[k][c]                     (c over the 4T table scalars)
-// with glyphs on the MMA M side (128 per TMEM accumulator, up to four accumulators per CTA) and the
-// coefficients on N (K padded to Kp, one MMA of N = Kp, or two of Kp / 2 above 256).  Operands:
+// with 128 glyphs on the MMA M side and the coefficients on N (K padded to Kp <= 128).  Operands:
 //   A = dlut tiles [128 glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
-//       the four converter warps into tf32 hi (overwriting the raw tile) and lo = tf32(x - hi);
+//       four converter warps into tf32 hi (overwriting the raw tile) and lo = tf32(x - hi);
 //   B = the transposed tf32 split of the basis, hiT / loT [Kp][4T] (part of shm_sh_basis's buffer).
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, as the forward bake).
-// The c range is split over the S CTAs of a thread-block cluster; at the end every CTA writes its
-// partial accumulators to shared memory and each CTA sums a slice of them over the cluster's ranks
-// in rank order through distributed shared memory, so the result does not depend on timing
-// (deterministic, no atomics, no workspace).
-//   warp 0 lane 0: TMA producer     warp 1: TMEM allocation, lane 0 issues the MMAs
-//   warps 4-7: tf32 split of each stage, then the epilogue (TMEM -> shared partials)
+// Accuracy: the error of the tensor cores' float32 accumulation grew with the length of the sum
+// kept in one TMEM accumulator (measured: 4.6e-5 of the largest entry after 434 stages, against
+// 7.9e-6 for a plain float32 sum).  So the MMAs accumulate CH stages at a time into one of two
+// TMEM buffers, and four drain warps add each finished chunk into float32 registers (one glyph row
+// per thread, Kp values) while the MMAs fill the other buffer.
+// Latency: seven 28 KB stages, and the producer prefetches dlut tiles into L2 PF stages ahead of
+// their shared-memory loads.
+// The c range may be split over the S CTAs of a thread-block cluster (small glyph counts); at the
+// end every CTA writes its register sums to shared memory and each CTA sums a slice of them over
+// the cluster's ranks in rank order through distributed shared memory, so the result does not
+// depend on timing (deterministic, no atomics, no workspace).
+//   warp 0 lane 0: TMA producer   warp 1: TMEM allocation, lane 0 issues the MMAs
+//   warps 4-7: drain (TMEM lane quadrant = warp % 4) and epilogue   warps 8-11: tf32 split
 // Every mbarrier wait is bounded (1 s) and raises SHM_DEV_TIMEOUT on expiry; the cluster barriers
 // are reached by every thread of every CTA the same number of times, aborted or not.
 namespace bwd {
 
-constexpr int MG = 128;                       // glyph rows per accumulator (MMA M)
+constexpr int MG = 128;                       // glyph rows (MMA M)
 constexpr uint32_t A_TILE = MG * KC * 4;      // 8 KB
-constexpr int MAX_ACC = 4;
+constexpr int KPMAX = 128;                    // register sums per drain thread
+constexpr int CH = 16;                        // stages per TMEM chunk
+constexpr int PF = 8;                         // stages of L2 prefetch ahead
+constexpr int THREADS = 384;
 constexpr uint32_t STAGE_CAP = 196 * 1024;    // shared memory for the stages (and the partials after them)
 constexpr uint32_t BAR_BYTES = 1024;
 
 struct Args {
     int M4;        // table scalars per glyph (4T), the reduction length
     int G, K, Kp;
-    int NB;        // N of one MMA
-    int nblk;      // MMAs per accumulator and K step (Kp = nblk NB)
-    int tgc;       // accumulators (glyph sub-tiles of 128) per CTA
     int S;         // CTAs per cluster (splits of the c range)
     int NC;        // stages over the whole c range
     int nstage;    // pipeline depth
-    uint32_t a_bytes, b_bytes, stage_bytes;
+    uint32_t b_bytes, stage_bytes;
     float* dcoeffs;
     int32_t* dev_status;
 };
@@ -64,6 +70,13 @@ __device__ __forceinline__ float ld_dsmem(uint32_t local_addr, uint32_t rank)
     return v;
 }
 
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* map, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"((uint64_t)map), "r"(x),
+                 "r"(y)
+                 : "memory");
+}
+
 __device__ __forceinline__ uint32_t idesc(int NB)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(MG >> 4) << 24);
@@ -79,7 +92,7 @@ __device__ __forceinline__ void mma_tf32_n(uint32_t d, uint64_t a, uint64_t b, u
         : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(THREADS, 1)
     k_sh_gemm_bwd_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBh,
                      const __grid_constant__ CUtensorMap mBl, Args a)
 {
@@ -87,23 +100,24 @@ __global__ void __launch_bounds__(256, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* bars = smem;
     uint8_t* stages = smem + BAR_BYTES;
-    const uint32_t full0 = smem_u32(bars), conv0 = full0 + 8 * 8, empty0 = conv0 + 8 * 8, tfull = empty0 + 8 * 8,
-                   drain = tfull + 8;
+    // barriers: full / conv / empty per stage (8 each at most), chunk full / empty per TMEM buffer
+    const uint32_t full0 = smem_u32(bars), conv0 = full0 + 64, empty0 = conv0 + 64, cfull0 = empty0 + 64,
+                   cempty0 = cfull0 + 16, drain = cempty0 + 16;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 512);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 520);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
-    const int group = blockIdx.x / a.S;
-    const int g_base = group * a.tgc * MG;
+    const int g_base = (blockIdx.x / a.S) * MG;
     const int c0 = (int)(((int64_t)a.NC * rank) / a.S), c1 = (int)(((int64_t)a.NC * (rank + 1)) / a.S);
     const int nst = c1 - c0;
-    const uint32_t ID = idesc(a.NB);
+    const int nchunk = (nst + CH - 1) / CH;
+    const uint32_t ID = idesc(a.Kp);
 
     auto stA = [&](int st) { return stages + (size_t)st * a.stage_bytes; };
-    auto stAlo = [&](int st) { return stages + (size_t)st * a.stage_bytes + a.a_bytes; };
-    auto stBh = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * a.a_bytes; };
-    auto stBl = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * a.a_bytes + a.b_bytes; };
+    auto stAlo = [&](int st) { return stages + (size_t)st * a.stage_bytes + A_TILE; };
+    auto stBh = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * A_TILE; };
+    auto stBl = [&](int st) { return stages + (size_t)st * a.stage_bytes + 2 * A_TILE + a.b_bytes; };
 
     if (threadIdx.x == 0) {
         for (int st = 0; st < a.nstage; ++st) {
@@ -111,7 +125,10 @@ __global__ void __launch_bounds__(256, 1)
             mbar_init(conv0 + 8 * st, 128);
             mbar_init(empty0 + 8 * st, 1);
         }
-        mbar_init(tfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(cfull0 + 8 * b, 1);
+            mbar_init(cempty0 + 8 * b, 128);
+        }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -119,7 +136,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(TMEM_COLS)
+                     "r"(256u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -127,22 +144,25 @@ __global__ void __launch_bounds__(256, 1)
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_holder;
+    float acc[KPMAX];  // drain warps: the glyph row's running sums
+#pragma unroll
+    for (int i = 0; i < KPMAX; ++i) acc[i] = 0.0f;
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA producer
+        for (int p = 0; p < PF && p < nst; ++p) tma_prefetch_l2(&mA, (c0 + p) * KC, g_base);
         int it = 0;
         for (; it < nst; ++it) {
             const int st = it % a.nstage;
             const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
             if (!mbar_wait(empty0 + 8 * st, ph ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
+            if (it + PF < nst) tma_prefetch_l2(&mA, (c0 + it + PF) * KC, g_base);
             const uint32_t fb = full0 + 8 * st;
             const int c = (c0 + it) * KC;
-            mbar_expect_tx(fb, a.a_bytes + 2 * a.b_bytes);
-            for (int q = 0; q < a.tgc; ++q) tma_load_2d(smem_u32(stA(st) + q * A_TILE), &mA, c, g_base + q * MG, fb);
-            for (int b = 0; b < a.nblk; ++b) {
-                tma_load_2d(smem_u32(stBh(st) + b * a.NB * KC * 4), &mBh, c, b * a.NB, fb);
-                tma_load_2d(smem_u32(stBl(st) + b * a.NB * KC * 4), &mBl, c, b * a.NB, fb);
-            }
+            mbar_expect_tx(fb, A_TILE + 2 * a.b_bytes);
+            tma_load_2d(smem_u32(stA(st)), &mA, c, g_base, fb);
+            tma_load_2d(smem_u32(stBh(st)), &mBh, c, 0, fb);
+            tma_load_2d(smem_u32(stBl(st)), &mBl, c, 0, fb);
         }
         if (it < nst) {
             // aborted: the last load issued into each stage must land before the shared memory is reused
@@ -157,46 +177,49 @@ __global__ void __launch_bounds__(256, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
         bool ok = true, any = false;
-        for (int it = 0; it < nst; ++it) {
-            const int st = it % a.nstage;
-            const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
-            if (!mbar_wait(conv0 + 8 * st, ph, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+        int it = 0;
+        for (int j = 0; j < nchunk && ok; ++j) {
+            const int b = j & 1;
+            if (!mbar_wait(cempty0 + 8 * b, ((uint32_t)(j >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
             fence_after();
-            for (int q = 0; q < a.tgc; ++q) {
-                const uint32_t ah = smem_u32(stA(st) + q * A_TILE), al = smem_u32(stAlo(st) + q * A_TILE);
-                for (int b = 0; b < a.nblk; ++b) {
-                    const uint32_t d = tmem + (uint32_t)(q * a.Kp + b * a.NB);
-                    const uint32_t bh = smem_u32(stBh(st) + b * a.NB * KC * 4), bl = smem_u32(stBl(st) + b * a.NB * KC * 4);
+            const uint32_t d = tmem + (uint32_t)(b * a.Kp);
+            const int jend = min(nst, (j + 1) * CH);
+            for (; it < jend; ++it) {
+                const int st = it % a.nstage;
+                const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
+                if (!mbar_wait(conv0 + 8 * st, ph, abort_flag, WAIT_LIMIT_NS)) { ok = false; break; }
+                fence_after();
+                const uint32_t ah = smem_u32(stA(st)), al = smem_u32(stAlo(st));
+                const uint32_t bh = smem_u32(stBh(st)), bl = smem_u32(stBl(st));
 #pragma unroll
-                    for (int kk = 0; kk < KC / 8; ++kk) {
-                        const uint32_t o = kk * 32;
-                        mma_tf32_n(d, sdesc(ah + o), sdesc(bh + o), ID, (it | kk) != 0);
-                        mma_tf32_n(d, sdesc(ah + o), sdesc(bl + o), ID, 1);
-                        mma_tf32_n(d, sdesc(al + o), sdesc(bh + o), ID, 1);
-                    }
+                for (int kk = 0; kk < KC / 8; ++kk) {
+                    const uint32_t o = kk * 32;
+                    mma_tf32_n(d, sdesc(ah + o), sdesc(bh + o), ID, (it != j * CH || kk != 0) ? 1u : 0u);
+                    mma_tf32_n(d, sdesc(ah + o), sdesc(bl + o), ID, 1);
+                    mma_tf32_n(d, sdesc(al + o), sdesc(bh + o), ID, 1);
                 }
+                any = true;
+                mma_commit(empty0 + 8 * st);
             }
-            any = true;
-            mma_commit(empty0 + 8 * st);
+            if (ok) mma_commit(cfull0 + 8 * b);
         }
-        if (ok) {
-            mma_commit(tfull);
-        } else if (any) {
+        if (!ok && any) {
             mma_commit(drain);
             const uint64_t t0 = globaltimer();
             while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
             }
         }
-    } else if (warp >= 4) {
+    } else if (warp >= 8) {
         // ---------------------------------------------------------------- tf32 split of each stage
-        const int t = threadIdx.x - 128;
-        const int n4 = (int)(a.a_bytes / 16);
+        const int t = threadIdx.x - 256;
+        constexpr int n4 = (int)(A_TILE / 16);
         for (int it = 0; it < nst; ++it) {
             const int st = it % a.nstage;
             const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
             if (!mbar_wait(full0 + 8 * st, ph, abort_flag, WAIT_LIMIT_NS)) break;
             float4* hi = reinterpret_cast<float4*>(stA(st));
             float4* lo = reinterpret_cast<float4*>(stAlo(st));
+#pragma unroll
             for (int i = t; i < n4; i += 128) {
                 const float4 x = hi[i];
                 float4 h, l;
@@ -208,50 +231,57 @@ __global__ void __launch_bounds__(256, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(conv0 + 8 * st);
         }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------------- drain: chunk sums -> registers
+        const int wq = warp & 3;
+        for (int j = 0; j < nchunk; ++j) {
+            const int b = j & 1;
+            if (!mbar_wait(cfull0 + 8 * b, (uint32_t)(j >> 1) & 1, abort_flag, WAIT_LIMIT_NS)) break;
+            fence_after();
+#pragma unroll
+            for (int cc = 0; cc < KPMAX; cc += 32) {
+                if (cc < a.Kp) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * a.Kp + cc), r);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) acc[cc + i] += __uint_as_float(r[i]);
+                }
+            }
+            fence_before();
+            mbar_arrive(cempty0 + 8 * b);
+        }
     }
     __syncthreads();
     // ---------------------------------------------------------------- epilogue: cluster reduction
-    if (warp >= 4 && !*abort_flag) {
-        if (!mbar_wait(tfull, 0, abort_flag, WAIT_LIMIT_NS)) *abort_flag = 1;
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
     const bool aborted = *abort_flag != 0;
-    float* P = reinterpret_cast<float*>(stages);  // [128][Kp + 1] partials of one accumulator
+    float* P = reinterpret_cast<float*>(stages);  // [128][Kp + 1] partial sums of this CTA
     const int PS = a.Kp + 1;
+    if (warp >= 4 && warp < 8 && !aborted) {
+        const int row = 32 * (warp & 3) + lane;
+#pragma unroll
+        for (int i = 0; i < KPMAX; ++i)
+            if (i < a.Kp) P[row * PS + i] = acc[i];
+    }
+    cluster_sync();
     const uint32_t P_s = smem_u32(P);
     const int E = MG * a.K;
     const int e0 = (int)(((int64_t)E * rank) / a.S), e1 = (int)(((int64_t)E * (rank + 1)) / a.S);
-    for (int q = 0; q < a.tgc; ++q) {
-        if (warp >= 4 && !aborted) {
-            const int wq = warp & 3, row = 32 * wq + lane;
-            for (int cc = 0; cc < a.Kp; cc += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(q * a.Kp + cc), r);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) P[row * PS + cc + i] = __uint_as_float(r[i]);
-            }
-        }
-        cluster_sync();
-        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int row = e / a.K, k = e - row * a.K;
-            const int g = g_base + q * MG + row;
-            float sum = 0.0f;
-            for (int rr = 0; rr < a.S; ++rr) sum += ld_dsmem(P_s + 4u * (uint32_t)(row * PS + k), (uint32_t)rr);
-            if (g < a.G && !aborted) a.dcoeffs[(int64_t)g * a.K + k] = sum;
-        }
-        cluster_sync();
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int row = e / a.K, k = e - row * a.K;
+        const int g = g_base + row;
+        float sum = 0.0f;
+        for (int rr = 0; rr < a.S; ++rr) sum += ld_dsmem(P_s + 4u * (uint32_t)(row * PS + k), (uint32_t)rr);
+        if (g < a.G && !aborted) a.dcoeffs[(int64_t)g * a.K + k] = sum;
     }
+    cluster_sync();
     if (threadIdx.x == 0 && aborted && a.dev_status) atomicOr(a.dev_status, SHM_DEV_TIMEOUT);
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u) : "memory");
     }
 }
 
-// c (Kp x M4) transposed tf32 split of the basis: hiT[k][c] = tf32(full[k][c]), loT = tf32(full - hi),
-// rows k >= K zero.
+// Transposed tf32 split of the basis: hiT[k][c] = tf32(full[k][c]), loT = tf32(full - hi), rows k >= K zero.
 __global__ void k_split_basis_t(const float* __restrict__ full, int K, int Kp, int64_t M4, float* __restrict__ hiT,
                                 float* __restrict__ loT)
 {
@@ -285,24 +315,15 @@ static bool plan(int G, int K, int Kp, int M4, int sms, int max_cluster, Args* o
 {
     Args a{};
     a.M4 = M4; a.G = G; a.K = K; a.Kp = Kp;
-    if (Kp > 512) return false;
-    a.nblk = Kp > 256 ? 2 : 1;
-    a.NB = Kp / a.nblk;
-    if (a.NB % 16 != 0 || a.NB > 256) return false;
-    a.tgc = 512 / Kp;
-    if (a.tgc > MAX_ACC) a.tgc = MAX_ACC;
-    if (a.tgc < 1) return false;
-    // fewer glyphs per CTA while even the largest clusters could not fill the SMs
-    while (a.tgc > 1 && (int64_t)((G + a.tgc * MG - 1) / (a.tgc * MG)) * max_cluster < sms) --a.tgc;
-    const int groups = (G + a.tgc * MG - 1) / (a.tgc * MG);
+    if (Kp > KPMAX || Kp % 16 != 0) return false;
+    const int groups = (G + MG - 1) / MG;
     a.S = sms / groups;
     if (a.S > max_cluster) a.S = max_cluster;
     if (a.S < 1) a.S = 1;
     a.NC = (M4 + KC - 1) / KC;
     if (a.S > a.NC) a.S = a.NC;
-    a.a_bytes = (uint32_t)a.tgc * A_TILE;
     a.b_bytes = (uint32_t)Kp * KC * 4;
-    a.stage_bytes = 2 * a.a_bytes + 2 * a.b_bytes;
+    a.stage_bytes = 2 * A_TILE + 2 * a.b_bytes;
     a.nstage = (int)(STAGE_CAP / a.stage_bytes);
     if (a.nstage > 8) a.nstage = 8;
     if (a.nstage < 2) return false;
@@ -347,7 +368,7 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
             cudaSuccess) {
             cudaLaunchConfig_t q = {};
             q.gridDim = dim3(16, 1, 1);
-            q.blockDim = dim3(256, 1, 1);
+            q.blockDim = dim3(THREADS, 1, 1);
             q.dynamicSmemBytes = 1024 + BAR_BYTES + STAGE_CAP;
             cudaLaunchAttribute at;
             at.id = cudaLaunchAttributeClusterDimension;
@@ -365,14 +386,14 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     Args a;
     if (!plan(G, K, Kp, M4, sm_count(), max_cluster, &a)) return cudaErrorNotSupported;
     CUtensorMap mA, mBh, mBl;
-    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, a.NB) || !make_map_c(&mBl, loT, Kp, M4, a.NB))
+    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, Kp) || !make_map_c(&mBl, loT, Kp, M4, Kp))
         return cudaErrorNotSupported;
     a.dcoeffs = dcoeffs;
     a.dev_status = dev_status;
-    const int groups = (G + a.tgc * MG - 1) / (a.tgc * MG);
+    const int groups = (G + MG - 1) / MG;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(groups * a.S), 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = 1024 + BAR_BYTES + (size_t)a.nstage * a.stage_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr;
