@@ -37,7 +37,7 @@ class RaycastParams(C.Structure):
     _fields_ = [("march", C.c_int), ("bisect", C.c_int), ("newton", C.c_int),
                 ("ambient", C.c_double), ("kd", C.c_double), ("ks", C.c_double),
                 ("shininess", C.c_double), ("light", C.c_double * 3),
-                ("lod", C.c_int), ("bisect_min", C.c_int), ("newton_min", C.c_int)]
+                ("lod", C.c_int), ("bisect_min", C.c_int), ("newton_min", C.c_int), ("recon", C.c_int)]
 
 
 class QueryOut(C.Structure):
@@ -425,8 +425,11 @@ def make_camera(eye, fwd, right, up, fov_y_deg, W, H):
 
 
 def make_raycast_params(march=32, bisect=12, newton=3, ambient=0.1, kd=0.7, ks=0.3, shininess=64.0,
-                        light=(1.0, 1.0, 1.0), lod=0, bisect_min=8, newton_min=2):
+                        light=(1.0, 1.0, 1.0), lod=0, bisect_min=8, newton_min=2, recon=-1):
+    """recon = -1: Hermite tables; else a RECON_* baseline on value grids (raycast's pool is then a
+    value pool from make_value_pool)."""
     p = RaycastParams()
+    p.recon = recon
     p.march, p.bisect, p.newton = march, bisect, newton
     p.lod, p.bisect_min, p.newton_min = lod, bisect_min, newton_min
     p.ambient, p.kd, p.ks, p.shininess = ambient, kd, ks, shininess

@@ -131,6 +131,8 @@ typedef struct {
     double ambient, kd, ks, shininess;
     double light[3];
     int lod, bisect_min, newton_min; /* projected-size refinement allocation (§3.1); lod = 0: fixed */
+    int recon; /* -1: Hermite tables (pool in records, §3.3); else a SHMO_RECON_* value-only baseline on
+                  value grids (pool in scalars, §4.5 equal-storage comparison) */
 } shmo_raycast_params;
 void shmo_lod_steps(const shmo_camera* cam, const shmo_raycast_params* prm, const double centre[3], double rmax,
                     int* bisect, int* newton, float* p_px);

@@ -17,6 +17,8 @@
  * max(n.l, 0) + ks max(n.h, 0)^shininess, white albedo, light direction `light`.
  * `margin` = min |F(t_k)| over all march samples of the pixel: pixels with a small margin may
  * legitimately resolve a different root under a different rounding of F.
+ * With prm->recon >= 0 the surface is the value-only baseline reconstruction of recon.c on value
+ * grids instead of the Hermite query, everything else unchanged (§4.5 equal-storage renders).
  *
  * Camera: d = normalise(fwd + x_ndc tan(fov_y/2) (W/H) right + y_ndc tan(fov_y/2) up) with
  * x_ndc = 2(px + 1/2)/W - 1 and y_ndc = 1 - 2(py + 1/2)/H.
@@ -36,7 +38,17 @@ typedef struct {
     const int64_t* off;
     const int32_t* Ns;
     const double* r0;
+    int recon;
 } lut_ref;
+
+/* R and its S^2 gradient at direction x of glyph g: the Hermite query (§3.3-§3.4), or for the
+ * equal-storage comparison (§4.5) a value-only baseline reconstruction of the glyph's value grid. */
+static void eval_surface(const lut_ref* L, int g, const double x[3], shmo_query_out* qo)
+{
+    double r0 = L->r0 ? L->r0[g] : 0.0;
+    if (L->recon >= 0) shmo_recon_one(L->recon, L->pool + (size_t)L->off[g], L->Ns[g], r0, x, qo);
+    else shmo_query_one(L->pool + (size_t)L->off[g] * 4, L->Ns[g], r0, x, qo);
+}
 
 /* F(p(t)) and dF/dt for one object. */
 static void surface_F(const lut_ref* L, int g, double scale, const double c[3], const double o[3],
@@ -44,7 +56,7 @@ static void surface_F(const lut_ref* L, int g, double scale, const double c[3], 
 {
     double x[3] = {o[0] + t * d[0] - c[0], o[1] + t * d[1] - c[1], o[2] + t * d[2] - c[2]};
     double dist = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-    shmo_query_one(L->pool + (size_t)L->off[g] * 4, L->Ns[g], L->r0 ? L->r0[g] : 0.0, x, qo);
+    eval_surface(L, g, x, qo);
     double sg = (qo->R >= 0.0) ? 1.0 : -1.0;
     double R = scale * fabs(qo->R);
     *F = dist - R;
@@ -84,7 +96,7 @@ void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* N
                         int px, int py, double rgba[4], double* depth, double normal[3],
                         int32_t* obj_id, double* margin)
 {
-    lut_ref L = {pool, off, Ns, r0};
+    lut_ref L = {pool, off, Ns, r0, prm->recon};
     double aspect = (double)cam->W / (double)cam->H;
     double xn = (2.0 * (px + 0.5) / cam->W - 1.0) * cam->tan_half_fov_y * aspect;
     double yn = (1.0 - 2.0 * (py + 0.5) / cam->H) * cam->tan_half_fov_y;
@@ -164,8 +176,7 @@ void shmo_raycast_pixel(const double* pool, const int64_t* off, const int32_t* N
     double dist = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
     double w[3] = {x[0] / dist, x[1] / dist, x[2] / dist};
     shmo_query_out qo;
-    int g = glyph[best];
-    shmo_query_one(pool + (size_t)off[g] * 4, Ns[g], r0 ? r0[g] : 0.0, x, &qo);
+    eval_surface(&L, glyph[best], x, &qo);
     double sg = (qo.R >= 0.0) ? 1.0 : -1.0;
     double R = scale[best] * fabs(qo.R);
     double gr[3] = {scale[best] * sg * qo.grad[0], scale[best] * sg * qo.grad[1], scale[best] * sg * qo.grad[2]};

@@ -60,6 +60,39 @@ def test_sphere_closed_form(oracle):
     assert hits > 50
 
 
+def test_value_only_sphere_closed_form(oracle):
+    """The value-only baselines (§4.5) reproduce a constant exactly (bilinear and Catmull-Rom weights
+    sum to one, their derivative weights to zero), so on a constant-radius value grid the ray caster's
+    recon mode must hit the analytic sphere with the radial normal, like the Hermite path."""
+    N = 8
+    grid = np.full((6, N + 4, N + 4), 0.75)
+    pool, off, Ns = oracle.make_value_pool([grid])
+    centre = np.array([[0.3, -0.2, 0.0]])
+    W, H = 32, 24
+    cam, frame = _camera(oracle, W, H)
+    R = 1.2
+    for method in (oracle.RECON_BILINEAR, oracle.RECON_BICUBIC):
+        prm = oracle.make_raycast_params(recon=method)
+        out = oracle.raycast(pool, off, Ns, centre, [1.2], [1.5], [0], cam, prm, r0=np.array([0.25]))
+        hits = 0
+        for q in range(W * H):
+            px, py = q % W, q // W
+            o, d = _ray(frame, W, H, px, py)
+            oc = o - centre[0]
+            b = oc @ d
+            disc = b * b - (oc @ oc - R * R)
+            if disc <= 1e-6:
+                assert out["obj_id"][q] == -1 or disc > -1e-6
+                continue
+            t = -b - math.sqrt(disc)
+            assert out["obj_id"][q] == 0
+            assert abs(out["depth"][q] - t) < 1e-9
+            p = o + t * d
+            assert np.allclose(out["normal"][q], (p - centre[0]) / R, atol=1e-7)
+            hits += 1
+        assert hits > 50
+
+
 def _bump_scene(oracle, N=16):
     counts, offs, mu, amp, width = I.bump_params(2, 40)
     luts = []
