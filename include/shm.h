@@ -357,6 +357,10 @@ typedef struct {
     int32_t lod;
     int32_t bisect_min;
     int32_t newton_min;
+    /* Value-only tables (SHM_LAYOUT_VALUE) only: the SHM_RECON_* baseline that reconstructs the
+     * surface and its gradient instead of the Hermite query (the equal-storage comparison renders of
+     * §4.5); ignored for Hermite tables. */
+    int32_t recon;
 } shm_raycast_params;
 
 typedef struct {
@@ -375,7 +379,9 @@ int64_t shm_raycast_workspace_bytes(int32_t n_obj, int32_t W, int32_t H);
  * [t_min, t_max] is sampled `march` times, the first sample with F < 0 brackets the root of
  * F(x) = |x - c| - R(w), which is refined by `bisect` bisection and `newton` Newton steps;
  * the nearest hit is shaded Blinn-Phong with the analytic normal (§3.4, signed rule
- * grad R = s sign(r) grad r).  Outputs (row-major, may be NULL): rgba [H][W][4],
+ * grad R = s sign(r) grad r).  A SHM_LAYOUT_VALUE table is ray cast through the baseline
+ * reconstruction prm->recon instead (its value and gradient, §4.5; SHM_ERR_INVALID_ARG for an
+ * unknown method).  Outputs (row-major, may be NULL): rgba [H][W][4],
  * depth [H][W] (t, +inf on a miss), normal [H][W][3], obj_id [H][W] (-1 on a miss).
  * objs: device [n_obj]; cam, prm: HOST structs. */
 shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj,

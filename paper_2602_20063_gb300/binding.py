@@ -55,7 +55,7 @@ class c_camera(C.Structure):
 class c_raycast_params(C.Structure):
     _fields_ = [("march", C.c_int32), ("bisect", C.c_int32), ("newton", C.c_int32), ("ambient", C.c_float),
                 ("kd", C.c_float), ("ks", C.c_float), ("shininess", C.c_float), ("light", C.c_float * 3),
-                ("lod", C.c_int32), ("bisect_min", C.c_int32), ("newton_min", C.c_int32)]
+                ("lod", C.c_int32), ("bisect_min", C.c_int32), ("newton_min", C.c_int32), ("recon", C.c_int32)]
 
 
 class c_object(C.Structure):
@@ -533,8 +533,10 @@ def make_camera(eye, fwd, right, up, fov_y_deg: float, W: int, H: int) -> c_came
 
 
 def make_raycast_params(march=32, bisect=12, newton=3, ambient=0.1, kd=0.7, ks=0.3, shininess=64.0,
-                        light=(1.0, 1.0, 1.0), lod=0, bisect_min=8, newton_min=2) -> c_raycast_params:
+                        light=(1.0, 1.0, 1.0), lod=0, bisect_min=8, newton_min=2, recon=0) -> c_raycast_params:
+    """recon: the SHM_RECON_* baseline used when the table is SHM_LAYOUT_VALUE (ignored otherwise)."""
     p = c_raycast_params()
+    p.recon = recon
     p.march, p.bisect, p.newton = march, bisect, newton
     p.lod, p.bisect_min, p.newton_min = lod, bisect_min, newton_min
     p.ambient, p.kd, p.ks, p.shininess = ambient, kd, ks, shininess

@@ -587,8 +587,9 @@ shm_status shm_raycast(const shm_lut* lut, const shm_object* objs, int32_t n_obj
 {
     shm_status st = check_lut(lut);
     if (st != SHM_OK) return st;
-    if (!hermite_layout(lut->layout)) return SHM_ERR_UNSUPPORTED;
     if (!cam || !prm || n_obj < 0 || (n_obj > 0 && !objs)) return SHM_ERR_INVALID_ARG;
+    if (lut->layout == SHM_LAYOUT_VALUE && (prm->recon < SHM_RECON_NEAREST || prm->recon > SHM_RECON_FAST_BICUBIC))
+        return SHM_ERR_INVALID_ARG;
     if (cam->W <= 0 || cam->H <= 0 || cam->W > 65536 || cam->H > 65536) return SHM_ERR_INVALID_ARG;
     if (prm->march < 1 || prm->march > 4096 || prm->bisect < 0 || prm->bisect > 64 || prm->newton < 0 ||
         prm->newton > 64 ||

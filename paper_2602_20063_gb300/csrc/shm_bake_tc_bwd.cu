@@ -17,8 +17,9 @@ namespace tc {
 // 7.9e-6 for a plain float32 sum).  So the MMAs accumulate CH stages at a time into one of two
 // TMEM buffers, and four drain warps add each finished chunk into float32 registers (one glyph row
 // per thread, Kp values) while the MMAs fill the other buffer.
-// Latency: seven 28 KB stages, and the producer prefetches dlut tiles into L2 PF stages ahead of
-// their shared-memory loads.
+// Latency: seven 28 KB stages, and the producer prefetches dlut into L2 in boxes of 1 KB per glyph
+// row (16 stages), two boxes ahead of the shared-memory loads: the 128 rows of a tile lie 4T x 4 B
+// apart, so 64-byte pieces per row and stage would reach DRAM as scattered small requests.
 // The c range may be split over the S CTAs of a thread-block cluster (small glyph counts); at the
 // end every CTA writes its register sums to shared memory and each CTA sums a slice of them over
 // the cluster's ranks in rank order through distributed shared memory, so the result does not
@@ -33,7 +34,8 @@ constexpr int MG = 128;                       // glyph rows (MMA M)
 constexpr uint32_t A_TILE = MG * KC * 4;      // 8 KB
 constexpr int KPMAX = 128;                    // register sums per drain thread
 constexpr int CH = 16;                        // stages per TMEM chunk
-constexpr int PF = 8;                         // stages of L2 prefetch ahead
+constexpr int PFW = 16;                       // stages per L2 prefetch box (256 c: 1 KB of each glyph row)
+constexpr int PFA = 2;                        // prefetch boxes ahead of the shared-memory loads
 constexpr int THREADS = 384;
 constexpr uint32_t STAGE_CAP = 196 * 1024;    // shared memory for the stages (and the partials after them)
 constexpr uint32_t BAR_BYTES = 1024;
@@ -94,7 +96,7 @@ __device__ __forceinline__ void mma_tf32_n(uint32_t d, uint64_t a, uint64_t b, u
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_sh_gemm_bwd_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBh,
-                     const __grid_constant__ CUtensorMap mBl, Args a)
+                     const __grid_constant__ CUtensorMap mBl, const __grid_constant__ CUtensorMap mApf, Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -150,13 +152,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------------------- TMA producer
-        for (int p = 0; p < PF && p < nst; ++p) tma_prefetch_l2(&mA, (c0 + p) * KC, g_base);
+        for (int p = 0; p < PFA && p * PFW < nst; ++p) tma_prefetch_l2(&mApf, (c0 + p * PFW) * KC, g_base);
         int it = 0;
         for (; it < nst; ++it) {
             const int st = it % a.nstage;
             const uint32_t ph = (uint32_t)(it / a.nstage) & 1;
             if (!mbar_wait(empty0 + 8 * st, ph ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
-            if (it + PF < nst) tma_prefetch_l2(&mA, (c0 + it + PF) * KC, g_base);
+            if (it % PFW == 0 && it + PFA * PFW < nst) tma_prefetch_l2(&mApf, (c0 + it + PFA * PFW) * KC, g_base);
             const uint32_t fb = full0 + 8 * st;
             const int c = (c0 + it) * KC;
             mbar_expect_tx(fb, A_TILE + 2 * a.b_bytes);
@@ -295,18 +297,20 @@ __global__ void k_split_basis_t(const float* __restrict__ full, int K, int Kp, i
     }
 }
 
-// 2-D map over a row-major [rows][M4] f32 array, boxes of [box_rows][16 c], 64-byte swizzle.
-static bool make_map_c(CUtensorMap* m, const float* base, int rows, int M4, int box_rows)
+// 2-D map over a row-major [rows][M4] f32 array, boxes of [box_rows][box_c]: the operand loads use
+// box_c = 16 with the 64-byte swizzle of the MMA descriptors; the L2 prefetch boxes are unswizzled.
+static bool make_map_c(CUtensorMap* m, const float* base, int rows, int M4, int box_rows, int box_c = KC,
+                       bool swizzle = true)
 {
     EncodeFn enc = encode_fn();
     if (!enc || ((uintptr_t)base & 15u) != 0) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)M4, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)M4 * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_c, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Plan of the tensor-core adjoint for (G, K, Kp, M4) on `sms` SMs; false when it does not apply
@@ -385,8 +389,9 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     }
     Args a;
     if (!plan(G, K, Kp, M4, sm_count(), max_cluster, &a)) return cudaErrorNotSupported;
-    CUtensorMap mA, mBh, mBl;
-    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, Kp) || !make_map_c(&mBl, loT, Kp, M4, Kp))
+    CUtensorMap mA, mBh, mBl, mApf;
+    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, Kp) || !make_map_c(&mBl, loT, Kp, M4, Kp) ||
+        !make_map_c(&mApf, dlut, G, M4, MG, PFW * tc::KC, false))
         return cudaErrorNotSupported;
     a.dcoeffs = dcoeffs;
     a.dev_status = dev_status;
@@ -403,6 +408,6 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sh_gemm_bwd_tc, mA, mBh, mBl, a);
+    return cudaLaunchKernelEx(&cfg, k_sh_gemm_bwd_tc, mA, mBh, mBl, mApf, a);
 }
 }  // namespace shm

@@ -145,14 +145,25 @@ struct Surf {
     Vec3 grad;
 };
 
-template <int DT, int LAYOUT>
+// R and its S^2 gradient at direction x: the Hermite query (RECON < 0, §3.3-§3.4), or a value-only
+// baseline reconstruction of a SHM_LAYOUT_VALUE table (RECON = SHM_RECON_*, the equal-storage
+// renders of §4.5).
+template <int DT, int LAYOUT, int RECON>
+__device__ __forceinline__ bool eval_surface(const LutView& L, const GlyphRef& G, float x0, float x1, float x2,
+                                             QueryResult& qr, Chart& ch)
+{
+    if constexpr (RECON < 0) return query_one<DT, LAYOUT>(L, G, x0, x1, x2, qr, ch);
+    else return recon_one<RECON, DT>(L, G, x0, x1, x2, qr, ch);
+}
+
+template <int DT, int LAYOUT, int RECON>
 __device__ __forceinline__ bool surface_F(const LutView& L, const GlyphRef& G, float scale, const float* c, const float* o,
                                           const Vec3& d, float t, Surf& S)
 {
     const float x0 = o[0] + t * d.x - c[0], x1 = o[1] + t * d.y - c[1], x2 = o[2] + t * d.z - c[2];
     QueryResult qr;
     Chart ch;
-    if (!query_one<DT, LAYOUT>(L, G, x0, x1, x2, qr, ch)) return false;
+    if (!eval_surface<DT, LAYOUT, RECON>(L, G, x0, x1, x2, qr, ch)) return false;
     const float dist = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
     S.sgn = qr.R >= 0.0f ? 1.0f : -1.0f;
     S.R = scale * fabsf(qr.R);
@@ -166,12 +177,20 @@ __device__ __forceinline__ bool surface_F(const LutView& L, const GlyphRef& G, f
 }
 
 // F alone at t (march and bisection need only its sign): chart, cell, footprint and the Hermite
-// value, no derivatives.  Same value as surface_F's S.F.
-template <int DT, int LAYOUT>
+// value, no derivatives.  Same value as surface_F's S.F.  (Value-only baselines: their full
+// reconstruction, whose value is the same.)
+template <int DT, int LAYOUT, int RECON>
 __device__ __forceinline__ bool surface_value(const LutView& L, const GlyphRef& G, float scale, const float* c,
                                               const float* o, const Vec3& d, float t, float& F)
 {
     const float x0 = o[0] + t * d.x - c[0], x1 = o[1] + t * d.y - c[1], x2 = o[2] + t * d.z - c[2];
+    if constexpr (RECON >= 0) {
+        QueryResult qr;
+        Chart ch;
+        if (!eval_surface<DT, LAYOUT, RECON>(L, G, x0, x1, x2, qr, ch)) return false;
+        F = sqrtf(x0 * x0 + x1 * x1 + x2 * x2) - scale * fabsf(qr.R);
+        return true;
+    }
     Chart ch;
     if (!chart_of(x0, x1, x2, ch)) return false;
     int i, j;
@@ -207,7 +226,7 @@ __device__ __forceinline__ void lod_steps(const shm_raycast_params& prm, const s
     newton = (p >= 64.0f) ? prm.newton : prm.newton_min;
 }
 
-template <int DT, int LAYOUT>
+template <int DT, int LAYOUT, int RECON>
 __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object* __restrict__ objs, int n, shm_camera cam,
                                                     shm_raycast_params prm, const int32_t* __restrict__ counts,
                                                     const int32_t* __restrict__ lists, uint32_t* tile_counter,
@@ -268,7 +287,7 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
             Surf S;
             float thit = qnan;
             float F;
-            if (!surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t0, F)) { status |= SHM_DEV_NONFINITE; continue; }
+            if (!surface_value<DT, LAYOUT, RECON>(L, G, ob.scale, ob.centre, o, d, t0, F)) { status |= SHM_DEV_NONFINITE; continue; }
             ++nq;
             if (F < 0.0f) {
                 thit = t0;
@@ -277,7 +296,7 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
                 bool found = false;
                 for (int k = 1; k <= prm.march; ++k) {
                     const float tk = t0 + (t1 - t0) * (float)k / (float)prm.march;
-                    surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, tk, F);
+                    surface_value<DT, LAYOUT, RECON>(L, G, ob.scale, ob.centre, o, d, tk, F);
                     ++nq;
                     if (F < 0.0f) {
                         lo = t0 + (t1 - t0) * (float)(k - 1) / (float)prm.march;
@@ -289,13 +308,13 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
                 if (!found) continue;
                 for (int it = 0; it < n_bisect; ++it) {
                     const float mid = 0.5f * (lo + hi);
-                    surface_value<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, mid, F);
+                    surface_value<DT, LAYOUT, RECON>(L, G, ob.scale, ob.centre, o, d, mid, F);
                     ++nq;
                     if (F < 0.0f) hi = mid; else lo = mid;
                 }
                 float t = 0.5f * (lo + hi);
                 for (int it = 0; it < n_newton; ++it) {
-                    surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, t, S);
+                    surface_F<DT, LAYOUT, RECON>(L, G, ob.scale, ob.centre, o, d, t, S);
                     ++nq;
                     if (S.dF == 0.0f) break;
                     const float tn = t - S.F / S.dF;
@@ -320,7 +339,7 @@ __global__ void __launch_bounds__(RT * RT) k_raycast(LutView L, const shm_object
         const shm_object ob = objs[best];
         const GlyphRef G = glyph_ref(L, ob.glyph);
         Surf S;
-        surface_F<DT, LAYOUT>(L, G, ob.scale, ob.centre, o, d, best_t, S);
+        surface_F<DT, LAYOUT, RECON>(L, G, ob.scale, ob.centre, o, d, best_t, S);
         ++nq;
         const float x0 = o[0] + best_t * d.x - ob.centre[0], x1 = o[1] + best_t * d.y - ob.centre[1],
                     x2 = o[2] + best_t * d.z - ob.centre[2];
@@ -368,9 +387,24 @@ cudaError_t launch_raycast(const LutView& L, const shm_object* objs, int n_obj, 
     uint32_t* tile_counter = (uint32_t*)base;
     unsigned long long* qc = (unsigned long long*)(base + 8);
 #define SHM_RC(DT, LY)                                                                                         \
-    k_raycast<DT, LY><<<blocks, RT * RT, 0, s>>>(L, objs, n_obj, cam, prm, counts, lists, tile_counter, qc, rgba, \
-                                                 depth, normal, obj_id, dev_status)
-    if (L.layout == SHM_LAYOUT_TEXEL) {
+    k_raycast<DT, LY, -1><<<blocks, RT * RT, 0, s>>>(L, objs, n_obj, cam, prm, counts, lists, tile_counter, qc,   \
+                                                     rgba, depth, normal, obj_id, dev_status)
+#define SHM_RV(DT, M)                                                                                          \
+    k_raycast<DT, SHM_LAYOUT_VALUE, M><<<blocks, RT * RT, 0, s>>>(L, objs, n_obj, cam, prm, counts, lists,      \
+                                                                  tile_counter, qc, rgba, depth, normal, obj_id, \
+                                                                  dev_status)
+#define SHM_RV_DT(M)                                 \
+    if (L.dtype == SHM_F32) SHM_RV(SHM_F32, M);      \
+    else if (L.dtype == SHM_F16) SHM_RV(SHM_F16, M); \
+    else SHM_RV(SHM_BF16, M)
+    if (L.layout == SHM_LAYOUT_VALUE) {
+        switch (prm.recon) {
+        case SHM_RECON_NEAREST: SHM_RV_DT(SHM_RECON_NEAREST); break;
+        case SHM_RECON_BILINEAR: SHM_RV_DT(SHM_RECON_BILINEAR); break;
+        case SHM_RECON_BICUBIC: SHM_RV_DT(SHM_RECON_BICUBIC); break;
+        default: SHM_RV_DT(SHM_RECON_FAST_BICUBIC); break;
+        }
+    } else if (L.layout == SHM_LAYOUT_TEXEL) {
         if (L.dtype == SHM_F32) SHM_RC(SHM_F32, SHM_LAYOUT_TEXEL);
         else if (L.dtype == SHM_F16) SHM_RC(SHM_F16, SHM_LAYOUT_TEXEL);
         else SHM_RC(SHM_BF16, SHM_LAYOUT_TEXEL);
@@ -380,6 +414,8 @@ cudaError_t launch_raycast(const LutView& L, const shm_object* objs, int n_obj, 
         else SHM_RC(SHM_BF16, SHM_LAYOUT_CELL);
     }
 #undef SHM_RC
+#undef SHM_RV
+#undef SHM_RV_DT
     return cudaGetLastError();
 }
 

@@ -218,3 +218,37 @@ def test_lod_refinement_parity(S):
     _compare(out, ref, rmax, W, H, depth_abs=bracket, seam=seam)
     steps = {a[:2] for a in alloc}
     assert len(steps) >= 3   # the scene exercises several allocations, Newton counts included
+
+
+@pytest.mark.parametrize("method", [1, 2])  # SHM_RECON_BILINEAR (FD normals), SHM_RECON_BICUBIC (Catmull-Rom)
+def test_value_only_raycast_parity(S, method):
+    """The value-only baselines ray cast (the equal-storage renders of §4.5): one L = 8 SH glyph as a
+    value table at 2N = 32 (the storage of a Hermite table at N = 16), device vs the oracle's value-only
+    ray caster on identical stored values, with the same bars as the Hermite renders (face seams
+    excluded: each face's gutter is evaluated in its own chart)."""
+    c = I.sh_coeffs(1, 8, 20063 + 41)[0]
+    N2 = 32
+    grid = O.value_grid_sh(N2, 8, c).astype(np.float32)
+    L = S.alloc_lut(1, N2, S.SHM_F32, S.SHM_LAYOUT_VALUE)
+    L.data.copy_(torch.from_numpy(grid.ravel()))
+    stored = grid.astype(np.float64)
+    rmax = np.array([1.3 * float(np.abs(stored).max())])
+    centres = np.zeros((1, 3))
+    objs = S.objects_tensor(centres, [1.0], rmax.astype(np.float32), [0])
+    W, H, fov = 96, 72, 40.0
+    eye, fwd, right, up = camera_frame((0.4, 0.5, 3.6))
+    out = S.raycast(L, objs, 1, S.make_camera(eye, fwd, right, up, fov, W, H), S.make_raycast_params(recon=method))
+    torch.cuda.synchronize()
+    pool, off, Ns = O.make_value_pool([stored.reshape(6, N2 + 4, N2 + 4)])
+    ref = O.raycast(pool, off, Ns, centres, [1.0], rmax, [0], O.make_camera(eye, fwd, right, up, fov, W, H),
+                    O.make_raycast_params(recon=method))
+    seam = _seam_pixels(ref, centres, eye, fwd, right, up, fov, W, H)
+    assert _compare(out, ref, rmax, W, H, seam=seam) > 500
+
+
+def test_value_only_raycast_rejects_unknown_method(S):
+    L = S.alloc_lut(1, 8, S.SHM_F32, S.SHM_LAYOUT_VALUE, zero=True)
+    objs = S.objects_tensor(np.zeros((1, 3)), [1.0], [1.0], [0])
+    eye, fwd, right, up = camera_frame((0.0, 0.0, 4.0))
+    with pytest.raises(S.ShmError, match="invalid"):
+        S.raycast(L, objs, 1, S.make_camera(eye, fwd, right, up, 40.0, 16, 16), S.make_raycast_params(recon=7))
