@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hermite value+grad queries/s, % of HBM roofline; fwd+bwd vs plain at fixed error"
-E2E_WARMUP, E2E_REPEATS, E2E_STEPS = 5, 3, 20
+E2E_WARMUP, E2E_REPEATS, E2E_STEPS = 5, 7, 20
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 
 
