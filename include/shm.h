@@ -225,7 +225,8 @@ typedef struct {
 } shm_source;
 
 /* Bytes of the SH bake basis for resolution N and degree L (host): K = (L+1)^2, M = 4*6(N+2)^2
- * table scalars per glyph, Kp = K rounded up to a multiple of 32; 4 * (K*M + 4*M*Kp). */
+ * table scalars per glyph, Kp = K rounded up to a multiple of 32, M16 = M rounded up to a multiple
+ * of 16; 4 * (K*M + 2*M*Kp + 2*M16*Kp). */
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
 
 /* Fills `basis` (device, shm_sh_basis_bytes) with every real SH function's record
@@ -234,8 +235,10 @@ int64_t shm_sh_basis_bytes(int32_t N, int32_t L);
  * coefficients c is then lut = sum_k c_k basis_k.  Layout (float32): full [K][M] (row k =
  * basis_k's table, texel-major, channel innermost), then hi [M][Kp] and lo [M][Kp] with
  * hi = tf32(full^T), lo = tf32(full^T - hi), zero for k >= K (operands of the tensor-core bake),
- * then hiT [Kp][M] and loT [Kp][M], the same split untransposed (rows k >= K zero; operands of the
- * tensor-core adjoint of shm_build_lut_backward).  Compute once per (N, L) and reuse. */
+ * then hiS and loS [M16/16][Kp][16], the same split untransposed in slabs of 16 columns (operands
+ * of the tensor-core adjoint of shm_build_lut_backward, one contiguous 64-byte-swizzled tile per
+ * slab): entry (k, c) at (c/16)*16*Kp + 16k + 4(((c%16)/4) XOR ((k/2)%4)) + c%4, zero for k >= K
+ * and c >= M.  Compute once per (N, L) and reuse. */
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream);
 
 /* Workspace bytes that select the tensor-core engine of shm_build_lut for (lut, src): for SH

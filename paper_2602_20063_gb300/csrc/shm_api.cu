@@ -356,8 +356,9 @@ shm_status shm_l2_fetch_granularity(int32_t bytes, int32_t* previous)
 int64_t shm_sh_basis_bytes(int32_t N, int32_t L)
 {
     if (N < 1 || L < 0 || L > 20) return -1;
-    const int64_t K = (int64_t)(L + 1) * (L + 1), M = 4LL * 6 * (N + 2) * (N + 2);
-    return (K * M + 4 * M * sh_kpad(L)) * (int64_t)sizeof(float);
+    const int64_t K = (int64_t)(L + 1) * (L + 1), M = 4LL * 6 * (N + 2) * (N + 2), Kp = sh_kpad(L);
+    const int64_t M16 = (M + 15) / 16 * 16;  // the adjoint's slabs cover M rounded up to 16 columns
+    return (K * M + 2 * M * Kp + 2 * M16 * Kp) * (int64_t)sizeof(float);
 }
 
 shm_status shm_sh_basis(int32_t N, int32_t L, float* basis, shm_stream stream)

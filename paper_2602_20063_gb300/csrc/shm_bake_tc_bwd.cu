@@ -9,8 +9,12 @@ namespace tc {
 //     dcoeffs[g][k] = sum_c dlut[g][c] basis[k][c]                     (c over the 4T table scalars)
 // with 128 glyphs on the MMA M side and the coefficients on N (K padded to Kp <= 128).  Operands:
 //   A = dlut tiles [128 glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
-//       four converter warps into tf32 hi (overwriting the raw tile) and lo = tf32(x - hi);
-//   B = the transposed tf32 split of the basis, hiT / loT [Kp][4T] (part of shm_sh_basis's buffer).
+//       four converter warps into tf32 hi = x truncated (overwriting the raw tile) and
+//       lo = tf32_rna(x - hi);
+//   B = the transposed tf32 split of the basis, hiS / loS (part of shm_sh_basis's buffer), stored as
+//       one contiguous [Kp][16 c] slab per stage with its rows already in the 64-byte swizzled order
+//       that a tensor load would produce, so each stage's B tile is one plain bulk copy (a tensor
+//       load of [Kp][16] from a [Kp][4T] array would be Kp separate 64-byte pieces).
 // D = A_hi B_hi + A_hi B_lo + A_lo B_hi (3xTF32, as the forward bake).
 // Accuracy: the error of the tensor cores' float32 accumulation grew with the length of the sum
 // kept in one TMEM accumulator (measured: 4.6e-5 of the largest entry after 434 stages, against
@@ -18,8 +22,8 @@ namespace tc {
 // TMEM buffers, and four drain warps add each finished chunk into float32 registers (one glyph row
 // per thread, Kp values) while the MMAs fill the other buffer.
 // Latency: seven 28 KB stages, and the producer prefetches dlut into L2 in boxes of 1 KB per glyph
-// row (16 stages), two boxes ahead of the shared-memory loads: the 128 rows of a tile lie 4T x 4 B
-// apart, so 64-byte pieces per row and stage would reach DRAM as scattered small requests.
+// row (16 stages), two boxes ahead of the shared-memory loads: the rows of a tile lie 4T x 4 B apart,
+// so 64-byte pieces per row and stage would reach DRAM as scattered small requests.
 // The c range may be split over the S CTAs of a thread-block cluster (small glyph counts); at the
 // end every CTA writes its register sums to shared memory and each CTA sums a slice of them over
 // the cluster's ranks in rank order through distributed shared memory, so the result does not
@@ -39,10 +43,15 @@ constexpr int PFA = 2;                        // prefetch boxes ahead of the sha
 constexpr int THREADS = 384;
 constexpr uint32_t STAGE_CAP = 196 * 1024;    // shared memory for the stages (and the partials after them)
 constexpr uint32_t BAR_BYTES = 1024;
+constexpr int MAXSTAGE = 8;
 
 struct Args {
+    const float* hiS;  // basis slabs, [NC][Kp][16] each, rows pre-swizzled
+    const float* loS;
     int M4;        // table scalars per glyph (4T), the reduction length
     int G, K, Kp;
+    int R;         // glyph rows per group (<= MG; the MMA's rows beyond R are never stored)
+    int groups;
     int S;         // CTAs per cluster (splits of the c range)
     int NC;        // stages over the whole c range
     int nstage;    // pipeline depth
@@ -50,6 +59,19 @@ struct Args {
     float* dcoeffs;
     int32_t* dev_status;
 };
+
+// Plain bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared memory,
+// completing on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// tf32 by truncation (the low 13 mantissa bits cleared): one logic operation where the rounding
+// conversion is a slower instruction; the remainder x - hi is exact and carries what was cut off.
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
 __device__ __forceinline__ uint32_t cluster_rank()
 {
@@ -95,22 +117,22 @@ __device__ __forceinline__ void mma_tf32_n(uint32_t d, uint64_t a, uint64_t b, u
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
-    k_sh_gemm_bwd_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mBh,
-                     const __grid_constant__ CUtensorMap mBl, const __grid_constant__ CUtensorMap mApf, Args a)
+    k_sh_gemm_bwd_tc(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mApf, Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* bars = smem;
     uint8_t* stages = smem + BAR_BYTES;
-    // barriers: full / conv / empty per stage (8 each at most), chunk full / empty per TMEM buffer
-    const uint32_t full0 = smem_u32(bars), conv0 = full0 + 64, empty0 = conv0 + 64, cfull0 = empty0 + 64,
-                   cempty0 = cfull0 + 16, drain = cempty0 + 16;
+    // barriers: full / conv / empty per stage (MAXSTAGE each at most), chunk full / empty per TMEM
+    // buffer, the drain barrier
+    const uint32_t full0 = smem_u32(bars), conv0 = full0 + 8 * MAXSTAGE, empty0 = conv0 + 8 * MAXSTAGE,
+                   cfull0 = empty0 + 8 * MAXSTAGE, cempty0 = cfull0 + 16, drain = cempty0 + 16;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 512);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 520);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_rank();
-    const int g_base = (blockIdx.x / a.S) * MG;
+    const int g_base = (blockIdx.x / a.S) * a.R;
     const int c0 = (int)(((int64_t)a.NC * rank) / a.S), c1 = (int)(((int64_t)a.NC * (rank + 1)) / a.S);
     const int nst = c1 - c0;
     const int nchunk = (nst + CH - 1) / CH;
@@ -161,10 +183,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (it % PFW == 0 && it + PFA * PFW < nst) tma_prefetch_l2(&mApf, (c0 + it + PFA * PFW) * KC, g_base);
             const uint32_t fb = full0 + 8 * st;
             const int c = (c0 + it) * KC;
-            mbar_expect_tx(fb, A_TILE + 2 * a.b_bytes);
+            mbar_expect_tx(fb, (uint32_t)a.R * KC * 4 + 2 * a.b_bytes);
             tma_load_2d(smem_u32(stA(st)), &mA, c, g_base, fb);
-            tma_load_2d(smem_u32(stBh(st)), &mBh, c, 0, fb);
-            tma_load_2d(smem_u32(stBl(st)), &mBl, c, 0, fb);
+            const size_t slab = (size_t)(c0 + it) * a.Kp * KC;
+            bulk_load(smem_u32(stBh(st)), a.hiS + slab, a.b_bytes, fb);
+            bulk_load(smem_u32(stBl(st)), a.loS + slab, a.b_bytes, fb);
         }
         if (it < nst) {
             // aborted: the last load issued into each stage must land before the shared memory is reused
@@ -225,7 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int i = t; i < n4; i += 128) {
                 const float4 x = hi[i];
                 float4 h, l;
-                h.x = tf32_rna(x.x); h.y = tf32_rna(x.y); h.z = tf32_rna(x.z); h.w = tf32_rna(x.w);
+                h.x = tf32_trunc(x.x); h.y = tf32_trunc(x.y); h.z = tf32_trunc(x.z); h.w = tf32_trunc(x.w);
                 l.x = tf32_rna(x.x - h.x); l.y = tf32_rna(x.y - h.y); l.z = tf32_rna(x.z - h.z); l.w = tf32_rna(x.w - h.w);
                 hi[i] = h;
                 lo[i] = l;
@@ -266,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     cluster_sync();
     const uint32_t P_s = smem_u32(P);
-    const int E = MG * a.K;
+    const int E = a.R * a.K;
     const int e0 = (int)(((int64_t)E * rank) / a.S), e1 = (int)(((int64_t)E * (rank + 1)) / a.S);
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int row = e / a.K, k = e - row * a.K;
@@ -283,17 +306,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// Transposed tf32 split of the basis: hiT[k][c] = tf32(full[k][c]), loT = tf32(full - hi), rows k >= K zero.
-__global__ void k_split_basis_t(const float* __restrict__ full, int K, int Kp, int64_t M4, float* __restrict__ hiT,
-                                float* __restrict__ loT)
+// tf32 split of the basis into the adjoint's slabs: entry (k, c) of slab s = c / 16 at
+// s*16*Kp + 16k + 4((c%16)/4 XOR (k/2)%4) + c%4 (16-byte chunks swizzled within each 64-byte row as
+// the 64-byte swizzle places them); hi = tf32(full[k][c]), lo = tf32(full - hi); rows k >= K and
+// columns c >= M4 of the last slab zero.
+__global__ void k_split_basis_t(const float* __restrict__ full, int K, int Kp, int64_t M4, float* __restrict__ hiS,
+                                float* __restrict__ loS)
 {
-    const int64_t n = (int64_t)Kp * M4;
+    const int64_t NC = (M4 + KC - 1) / KC;
+    const int64_t n = NC * Kp * KC;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = e / M4;
-        const float v = (k < K) ? __ldg(full + e) : 0.0f;
+        const int64_t slab = e / ((int64_t)Kp * KC);
+        const int r = (int)(e - slab * Kp * KC);
+        const int k = r / KC, q = r % KC;            // row and position within the stored row
+        const int cc = (((q >> 2) ^ ((k >> 1) & 3)) << 2) | (q & 3);  // logical column within the slab
+        const int64_t c = slab * KC + cc;
+        const float v = (k < K && c < M4) ? __ldg(full + (int64_t)k * M4 + c) : 0.0f;
         const float h = tf32_rna(v);
-        hiT[e] = h;
-        loT[e] = tf32_rna(v - h);
+        hiS[e] = h;
+        loS[e] = tf32_rna(v - h);
     }
 }
 
@@ -314,13 +345,22 @@ static bool make_map_c(CUtensorMap* m, const float* base, int rows, int M4, int 
 }
 
 // Plan of the tensor-core adjoint for (G, K, Kp, M4) on `sms` SMs; false when it does not apply
-// (the CUDA-core kernel is used then).
+// (the CUDA-core kernel is used then).  Glyph groups of R <= 128 rows: with at least 64 glyphs per
+// SM, R is chosen so that the groups fill whole waves of the SMs (16,384 glyphs on 152 SMs: 108
+// rows, 152 CTAs, where 128-row groups would leave 24 SMs idle); below that, 128-row groups whose c
+// range is split over the CTAs of a cluster.
 static bool plan(int G, int K, int Kp, int M4, int sms, int max_cluster, Args* out)
 {
     Args a{};
     a.M4 = M4; a.G = G; a.K = K; a.Kp = Kp;
     if (Kp > KPMAX || Kp % 16 != 0) return false;
-    const int groups = (G + MG - 1) / MG;
+    a.R = MG;
+    if ((int64_t)G >= 64LL * sms) {
+        const int64_t waves = ((int64_t)G + (int64_t)MG * sms - 1) / ((int64_t)MG * sms);
+        a.R = (int)(((int64_t)G + waves * sms - 1) / (waves * sms));
+    }
+    const int groups = (G + a.R - 1) / a.R;
+    a.groups = groups;
     a.S = sms / groups;
     if (a.S > max_cluster) a.S = max_cluster;
     if (a.S < 1) a.S = 1;
@@ -329,7 +369,7 @@ static bool plan(int G, int K, int Kp, int M4, int sms, int max_cluster, Args* o
     a.b_bytes = (uint32_t)Kp * KC * 4;
     a.stage_bytes = 2 * A_TILE + 2 * a.b_bytes;
     a.nstage = (int)(STAGE_CAP / a.stage_bytes);
-    if (a.nstage > 8) a.nstage = 8;
+    if (a.nstage > MAXSTAGE) a.nstage = MAXSTAGE;
     if (a.nstage < 2) return false;
     if ((uint64_t)MG * (Kp + 1) * 4 > (uint64_t)a.nstage * a.stage_bytes) return false;  // partials fit
     *out = a;
@@ -339,16 +379,16 @@ static bool plan(int G, int K, int Kp, int M4, int sms, int max_cluster, Args* o
 }  // namespace bwd
 }  // namespace tc
 
-// basis: [K][M] full, hi [M][Kp], lo [M][Kp], then the adjoint's hiT [Kp][M] and loT [Kp][M]
+// basis: [K][M] full, hi [M][Kp], lo [M][Kp], then the adjoint's slabs hiS and loS [NC][Kp][16]
 cudaError_t launch_basis_split_t(int N, int L, float* basis, cudaStream_t s)
 {
     const int K = (L + 1) * (L + 1), Kp = sh_kpad(L);
     const int64_t M = 4LL * 6 * (N + 2) * (N + 2);
-    float* hiT = basis + (int64_t)K * M + 2 * M * Kp;
-    float* loT = hiT + (int64_t)Kp * M;
-    const int64_t n = (int64_t)Kp * M;
-    tc::bwd::k_split_basis_t<<<(unsigned)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8), 256, 0, s>>>(
-        basis, K, Kp, M, hiT, loT);
+    const int64_t slabs = (M + tc::KC - 1) / tc::KC * tc::KC * Kp;
+    float* hiS = basis + (int64_t)K * M + 2 * M * Kp;
+    float* loS = hiS + slabs;
+    tc::bwd::k_split_basis_t<<<(unsigned)((slabs + 255) / 256 < 65535 * 8 ? (slabs + 255) / 256 : 65535 * 8), 256, 0,
+                               s>>>(basis, K, Kp, M, hiS, loS);
     return cudaGetLastError();
 }
 
@@ -360,8 +400,8 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     using namespace tc::bwd;
     const int K = (L + 1) * (L + 1), Kp = sh_kpad(L);
     const int M4 = 4 * 6 * (N + 2) * (N + 2);
-    const float* hiT = basis + (int64_t)K * M4 + 2LL * M4 * Kp;
-    const float* loT = hiT + (int64_t)Kp * M4;
+    const float* hiS = basis + (int64_t)K * M4 + 2LL * M4 * Kp;
+    const float* loS = hiS + ((int64_t)M4 + tc::KC - 1) / tc::KC * tc::KC * Kp;
     cudaError_t e = ensure_dynamic_smem((const void*)k_sh_gemm_bwd_tc, (int)(1024 + BAR_BYTES + STAGE_CAP));
     if (e != cudaSuccess) return e;
     // clusters of up to 16 CTAs where the device allows them, else the portable 8
@@ -389,15 +429,16 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     }
     Args a;
     if (!plan(G, K, Kp, M4, sm_count(), max_cluster, &a)) return cudaErrorNotSupported;
-    CUtensorMap mA, mBh, mBl, mApf;
-    if (!make_map_c(&mA, dlut, G, M4, MG) || !make_map_c(&mBh, hiT, Kp, M4, Kp) || !make_map_c(&mBl, loT, Kp, M4, Kp) ||
-        !make_map_c(&mApf, dlut, G, M4, MG, PFW * tc::KC, false))
+    CUtensorMap mA, mApf;
+    if (((uintptr_t)hiS & 15u) != 0 || !make_map_c(&mA, dlut, G, M4, a.R) ||
+        !make_map_c(&mApf, dlut, G, M4, a.R, PFW * tc::KC, false))
         return cudaErrorNotSupported;
+    a.hiS = hiS;
+    a.loS = loS;
     a.dcoeffs = dcoeffs;
     a.dev_status = dev_status;
-    const int groups = (G + MG - 1) / MG;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(groups * a.S), 1, 1);
+    cfg.gridDim = dim3((unsigned)(a.groups * a.S), 1, 1);
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = 1024 + BAR_BYTES + (size_t)a.nstage * a.stage_bytes;
     cfg.stream = s;
@@ -408,6 +449,6 @@ cudaError_t launch_sh_build_bwd_tc(int N, int G, int L, const float* dlut, const
     attr.val.clusterDim.z = 1;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sh_gemm_bwd_tc, mA, mBh, mBl, mApf, a);
+    return cudaLaunchKernelEx(&cfg, k_sh_gemm_bwd_tc, mA, mApf, a);
 }
 }  // namespace shm

@@ -45,8 +45,10 @@ def test_host_helpers(lib):
     assert lib.shm_records_per_glyph(0, 0) == -1
     assert lib.shm_record_bytes(0, 0) == 16 and lib.shm_record_bytes(2, 0) == 8 and lib.shm_record_bytes(0, 1) == 64
     M = 4 * 6 * 34 * 34
-    # full [K][M] + tf32 hi/lo [M][Kp] (bake operands) + hiT/loT [Kp][M] (adjoint operands)
+    # full [K][M] + tf32 hi/lo [M][Kp] (bake operands) + hi/lo slabs over M rounded up to 16 (adjoint operands)
     assert lib.shm_sh_basis_bytes(32, 8) == (81 * M + 4 * M * 96) * 4
+    M9 = 4 * 6 * 11 * 11
+    assert lib.shm_sh_basis_bytes(9, 8) == (81 * M9 + 2 * M9 * 96 + 2 * ((M9 + 15) // 16 * 16) * 96) * 4
     assert lib.shm_sh_basis_bytes(32, 21) == -1
     Ns = (C.c_int32 * 3)(16, 32, 5)
     offs = (C.c_int64 * 3)()

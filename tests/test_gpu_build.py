@@ -40,11 +40,20 @@ def _split_basis(buf, N, L):
 
 
 def _split_basis_t(buf, N, L):
-    """The adjoint's operands after the forward ones: hiT, loT [Kp][M]."""
+    """The adjoint's operands after the forward ones, slabs [M16/16][Kp][16] with each row's four
+    16-byte chunks permuted (chunk j of row k stored at j XOR (k/2)%4), unpacked to hiT, loT [Kp][M16]."""
     K, M = (L + 1) ** 2, 4 * 6 * (N + 2) ** 2
     Kp = (K + 31) // 32 * 32
+    M16 = (M + 15) // 16 * 16
     o = K * M + 2 * M * Kp
-    return buf[o:o + Kp * M].reshape(Kp, M), buf[o + Kp * M:o + 2 * Kp * M].reshape(Kp, M)
+    out = []
+    for part in range(2):
+        slabs = buf[o + part * M16 * Kp:o + (part + 1) * M16 * Kp].reshape(M16 // 16, Kp, 4, 4)
+        k = np.arange(Kp)[:, None]
+        src = np.arange(4)[None, :] ^ ((k >> 1) & 3)                 # stored chunk of logical chunk j
+        logical = np.take_along_axis(slabs, src[None, :, :, None].repeat(slabs.shape[0], 0), axis=2)
+        out.append(logical.reshape(M16 // 16, Kp, 16).transpose(1, 0, 2).reshape(Kp, M16))
+    return out[0], out[1]
 
 
 @pytest.mark.parametrize("N,L", [(10, 4), (32, 8), (7, 16)])
@@ -64,9 +73,10 @@ def test_sh_basis(S, N, L):
     assert np.all(np.abs(hi[:, :K] + lo[:, :K].astype(np.float64) - fT) <= 2.0 ** -21 * np.abs(fT))
     # the adjoint's untransposed split: the same values row by row, zero rows k >= K
     hiT, loT = _split_basis_t(buf, N, L)
-    assert buf.size == K * full.shape[1] + 4 * full.shape[1] * Kp
-    assert np.array_equal(hiT[:K], hi[:, :K].T) and np.array_equal(loT[:K], lo[:, :K].T)
-    assert np.all(hiT[K:] == 0) and np.all(loT[K:] == 0)
+    M = full.shape[1]
+    assert buf.size == K * M + 2 * M * Kp + 2 * ((M + 15) // 16 * 16) * Kp
+    assert np.array_equal(hiT[:K, :M], hi[:, :K].T) and np.array_equal(loT[:K, :M], lo[:, :K].T)
+    assert np.all(hiT[K:] == 0) and np.all(loT[K:] == 0) and np.all(hiT[:, M:] == 0) and np.all(loT[:, M:] == 0)
 
 
 @pytest.mark.parametrize("engine", ["simt", "tcgen05"])
