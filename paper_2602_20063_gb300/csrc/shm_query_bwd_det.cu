@@ -15,7 +15,8 @@
 // Chunks run in order inside the CTA, glyphs are disjoint, so the whole result is fixed.  Chunks of
 // 256 queries and four CTAs per SM (footprints read through L1/L2): with whole tables staged in
 // shared memory only two 1,024-thread CTAs fit per SM, which measured 5.7 ms against 4.7 ms on the
-// 2^26-query glyph field.
+// 2^26-query glyph field.  Sort keys are 32-bit (one shuffle per exchange) when every record index
+// of a uniform pool fits in 24 bits (N <= 1670), else 64-bit.
 #include "shm_bwd.cuh"
 
 namespace shm {
@@ -25,19 +26,19 @@ namespace {
 constexpr int DBLOCK = 256;
 constexpr int DBITS = 8;   // log2(DBLOCK): query slot in the low bits of the sort key
 constexpr int DMINB = 4;   // CTAs per SM
-constexpr uint64_t NO_KEY = ~0ull;
+// Shared memory: two key buffers [DBLOCK] of KT, then the payload [5][DBLOCK] f32.
+template <class KT>
+constexpr uint32_t det_smem() { return 2 * DBLOCK * sizeof(KT) + 5 * DBLOCK * 4; }
 
-// Shared memory: two key buffers [DBLOCK] u64, then the payload [5][DBLOCK] f32.
-constexpr uint32_t DET_SMEM = 2 * DBLOCK * 8 + 5 * DBLOCK * 4;
-
+template <class KT>
 struct DetEmit {
-    uint64_t key;
+    KT key;
     float* pay;  // [5][DBLOCK]: s, t, g_r, g_rs, g_rt
     int slot;
     __device__ __forceinline__ void operator()(int64_t rec, const Herm2&, const Herm2&, float s, float t, float g_r,
                                                float g_rs, float g_rt)
     {
-        key = ((uint64_t)rec << DBITS) | (uint64_t)slot;
+        key = ((KT)rec << DBITS) | (KT)slot;
         pay[slot] = s;
         pay[DBLOCK + slot] = t;
         pay[2 * DBLOCK + slot] = g_r;
@@ -46,31 +47,33 @@ struct DetEmit {
     }
 };
 
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
+__device__ __forceinline__ uint64_t shfl_xor_key(uint64_t v, int m)
 {
     const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
     const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
     return ((uint64_t)hi << 32) | lo;
 }
+__device__ __forceinline__ uint32_t shfl_xor_key(uint32_t v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
 // Ascending bitonic sort of the DBLOCK keys held one per thread (thread tid holds position tid).
 // Compare-exchange partners tid ^ j: by shuffles for j < 32, through shared memory otherwise, with
 // two buffers used in turn so that one barrier per shared stage suffices.  Returns the key at
 // position tid; the sorted keys are also left in `out` (one of the two buffers) after a barrier.
-__device__ __forceinline__ uint64_t bitonic_sort(uint64_t x, uint64_t* buf0, uint64_t* buf1, uint64_t*& out, int tid)
+template <class KT>
+__device__ __forceinline__ KT bitonic_sort(KT x, KT* buf0, KT* buf1, KT*& out, int tid)
 {
     int flip = 0;
     for (int k = 2; k <= DBLOCK; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            uint64_t y;
+            KT y;
             if (j >= 32) {
-                uint64_t* b = flip ? buf1 : buf0;
+                KT* b = flip ? buf1 : buf0;
                 flip ^= 1;
                 b[tid] = x;
                 __syncthreads();
                 y = b[tid ^ j];
             } else {
-                y = shfl_xor_u64(x, j);
+                y = shfl_xor_key(x, j);
             }
             const bool up = (tid & k) == 0, lower = (tid & j) == 0;
             x = (lower == up) ? (x < y ? x : y) : (x < y ? y : x);
@@ -82,14 +85,15 @@ __device__ __forceinline__ uint64_t bitonic_sort(uint64_t x, uint64_t* buf0, uin
     return x;
 }
 
-template <int DT, int LAYOUT>
+template <int DT, int LAYOUT, class KT>
 __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr KT NO_KEY = ~(KT)0;
     unsigned char* fixed = smem;
-    uint64_t* kbuf0 = reinterpret_cast<uint64_t*>(fixed);
-    uint64_t* kbuf1 = kbuf0 + DBLOCK;
-    float* pay = reinterpret_cast<float*>(fixed + 2 * DBLOCK * 8);
+    KT* kbuf0 = reinterpret_cast<KT*>(fixed);
+    KT* kbuf1 = kbuf0 + DBLOCK;
+    float* pay = reinterpret_cast<float*>(fixed + 2 * DBLOCK * sizeof(KT));
     const int tid = threadIdx.x;
     const int G = a.L.n_glyphs;
     uint32_t status = 0;
@@ -118,7 +122,7 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
         for (int64_t c0 = s0; c0 < s1; c0 += DBLOCK) {
             // 1. reverse math per query; key and payload into shared memory
             const int64_t q = c0 + tid;
-            DetEmit emit{NO_KEY, pay, tid};
+            DetEmit<KT> emit{NO_KEY, pay, tid};
             if (q < s1) {
                 float3 dd = make_float3(qnan, qnan, qnan);
                 const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
@@ -133,17 +137,17 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
             }
             // 2. group by cell, queries in order within a cell (the payload writes are ordered before
             //    the reads of step 3 by the sort's barriers)
-            uint64_t* key;
-            const uint64_t k = bitonic_sort(emit.key, kbuf0, kbuf1, key, tid);
+            KT* key;
+            const KT k = bitonic_sort<KT>(emit.key, kbuf0, kbuf1, key, tid);
             // 3. the first slot of each cell's run sums the run in query order
-            const uint64_t cell = k >> DBITS;
+            const KT cell = k >> DBITS;
             const bool head = (k != NO_KEY) && (tid == 0 || (key[tid - 1] >> DBITS) != cell);
             float4 acc[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) acc[m] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (head) {
                 for (int r = tid; r < DBLOCK; ++r) {
-                    const uint64_t kr = key[r];
+                    const KT kr = key[r];
                     if (kr == NO_KEY || (kr >> DBITS) != cell) break;
                     const int src = (int)(kr & (DBLOCK - 1));
                     const Herm2 A = herm2(pay[src]), B = herm2(pay[DBLOCK + src]);
@@ -177,17 +181,25 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
     report_status(a.dev_status, status);
 }
 
-template <int DT, int LAYOUT>
-cudaError_t launch_det_t(const BackwardArgs& a, cudaStream_t s)
+template <int DT, int LAYOUT, class KT>
+cudaError_t launch_det_k(const BackwardArgs& a, cudaStream_t s)
 {
-    const int smem = (int)DET_SMEM;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_query_bwd_det<DT, LAYOUT>, smem);
+    const int smem = (int)det_smem<KT>();
+    cudaError_t e = ensure_dynamic_smem((const void*)k_query_bwd_det<DT, LAYOUT, KT>, smem);
     if (e != cudaSuccess) return e;
     int64_t blocks = (int64_t)sm_count() * DMINB;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     if (blocks < 1) blocks = 1;
-    k_query_bwd_det<DT, LAYOUT><<<(unsigned)blocks, DBLOCK, smem, s>>>(a);
+    k_query_bwd_det<DT, LAYOUT, KT><<<(unsigned)blocks, DBLOCK, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <int DT, int LAYOUT>
+cudaError_t launch_det_t(const BackwardArgs& a, cudaStream_t s)
+{
+    // the gradient table is float32 texel layout: record indices below 6 (N + 2)^2 per glyph
+    const bool narrow = a.D.N_uniform > 0 && 6LL * (a.D.N_uniform + 2) * (a.D.N_uniform + 2) < (1LL << (32 - DBITS));
+    return narrow ? launch_det_k<DT, LAYOUT, uint32_t>(a, s) : launch_det_k<DT, LAYOUT, uint64_t>(a, s);
 }
 
 }  // namespace
