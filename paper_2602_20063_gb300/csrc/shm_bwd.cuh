@@ -104,7 +104,8 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
     const float Nf = (float)N;
     const float R = Gr.r0 + r, Ru = Nf * rs, Rv = Nf * rt;
     const float x = c.x, y = c.y;
-    const float rho = sqrtf(fmaf(x, x, fmaf(y, y, 1.0f)));
+    const float rho2 = fmaf(x, x, fmaf(y, y, 1.0f));
+    const float irho = rsqrtf(rho2), rho = rho2 * irho;  // reciprocal square root: no division below
     // tangent-frame components (a, b, c) = (sigma e_k, e_k1, e_k2)
     const float Va = -(x * Ru + y * Rv), Vb = Ru, Vc = Rv;
     const float il = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
@@ -153,8 +154,8 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
     const float grho = 0.5f * (Va * tGa + Vb * tGb + Vc * tGc);
     const float gRu = gVb - x * gVa;
     const float gRv = gVc - y * gVa;
-    const float gx = -Ru * gVa + grho * x / rho;
-    const float gy = -Rv * gVa + grho * y / rho;
+    const float gx = -Ru * gVa + grho * x * irho;
+    const float gy = -Rv * gVa + grho * y * irho;
     const float g_r = gRt, g_rs = Nf * gRu, g_rt = Nf * gRv;
     // table: the cell's corner weights go to the emitter (record index of corner (0,0) within the
     // glyph's texel table; corner (aa, bb) is record rec + bb P + aa)
@@ -164,8 +165,8 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
         const float gt = g_r * rt + g_rs * rst + g_rt * rtt;
         const float gxx = gx + gs * 0.5f * Nf, gyy = gy + gt * 0.5f * Nf;
         // chart coordinates -> d (frame components; a-component carries sigma)
-        float dA = -(x * gxx + y * gyy) / c.m;  // along a = sigma e_k
-        float dB = gxx / c.m, dC = gyy / c.m;
+        float dA = -(x * gxx + y * gyy) * c.im;  // along a = sigma e_k (c.im = 1/|d_k|)
+        float dB = gxx * c.im, dC = gyy * c.im;
         // w = d/|d|
         const float wdg = wk * gwa + w1 * gwb + w2 * gwc;
         dA += (gwa - wk * wdg) * il;
