@@ -407,7 +407,7 @@ class GlyphField:
         del dco
         ex["fwd_bwd"] = {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4), "fwd_plus_bwd_over_fwd": round((fwd + bwd) / fwd, 3),
                          "bwd_deterministic_ms": round(bwd_det, 4), "bake_bwd_ms": round(bake_bwd, 4),
-                         "note": "backward = recompute + 4 float4 atomics per query into a float32 texel table + d/ddirs; "
+                         "note": "backward = recompute + 4 float4 vector reductions per query (issued by lane pairs, one 32-byte footprint row per pair) into a float32 texel table + d/ddirs; "
                                  "deterministic = per-glyph CTA, chunks sorted by cell, per-cell sums added in a fixed order"}
         del dl
         ex["precision"] = self.precision_extras(S, torch, timeit, n, fwd)
