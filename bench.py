@@ -1264,7 +1264,19 @@ class Impostors:
         self.frame += 1
 
     def roofline_terms(self, peaks, ktot, sms):
-        return {}
+        """The ray cast is bound by instruction issue (SIMT root finding, DRAM ~5 %): its roofline is
+        the issue-slot ceiling, SMs x 4 schedulers x one warp instruction per clock at the maximum SM
+        clock, against the warp instructions of one k_raycast launch counted by the committed ncu
+        capture (same source only; the timed region also holds the rank and bin kernels)."""
+        files = ["paper_2602_20063_gb300/csrc/shm_raycast.cu", "paper_2602_20063_gb300/csrc/shm_device.cuh"]
+        p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+        e = json.load(open(p)).get("raycast") if os.path.exists(p) else None
+        if not e or e.get("source_hash") != source_hash(*files):
+            return {}
+        ceiling = sms * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12  # T warp instructions/s
+        return {"raycast": {"bound": "alu", "algorithmic": float(e["warp_instructions_per_launch"]),
+                            "unit": "T warp-inst/s", "peak": ceiling, "files": files,
+                            "per_unit": "warp instructions of the frame's ray cast (9.8 surface queries per pixel)"}}
 
     def extras(self, S, torch, steps):
         """Surface queries per frame, and the ray cast alone with fixed refinement counts against
@@ -1655,7 +1667,9 @@ def run_gpu(args):
             "unit": dk.get("unit"), "frac": dk.get("frac"),
             "traffic": load_traffic(dom, terms[dom]["files"]) if dom in terms else None,
             "peak_source": ("measured" if peaks["_source"] == "measured" else "fallback") +
-                           (" hbm_gbs" if dk.get("unit") == "GB/s" else " FP32 SIMT from unit counts x max clock")}
+                           (" hbm_gbs" if dk.get("unit") == "GB/s" else
+                            " issue slots from unit counts x max clock" if dk.get("unit") == "T warp-inst/s" else
+                            " FP32 SIMT from unit counts x max clock")}
     extras = {} if args.no_extras else work.extras(S, torch, args.steps)
     line = {"metric": METRIC, "value": value, "unit": work.unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
