@@ -5,8 +5,9 @@ oracle.
 The cases walk the segment loop through its edges: empty segments between non-empty ones, segments
 of 1, 511, 512, 513 and several blocks of queries, queries outside every segment (NaN d/ddirs and
 SHM_DEV_BOUNDS), more glyphs than CTAs, each subset of upstream gradients, 16-bit tables and the
-fused fit loss.  Tolerances as in the other adjoint tests: dlut within 2e-5 of each channel's
-largest magnitude, d/ddirs within 1e-4 of its largest magnitude away from cell edges.
+fused fit loss; and, on the unstaged pass, lane pairs whose paired gradient reductions straddle
+two glyphs of different N.  Tolerances as in the other adjoint tests: dlut within 2e-5 of each
+channel's largest magnitude, d/ddirs within 1e-4 of its largest magnitude away from cell edges.
 """
 import numpy as np
 import pytest
@@ -167,3 +168,40 @@ def test_staged_fit_backward(S):
     for name, (loss, dl) in out.items():
         assert abs(loss - lref) <= 1e-5 * lref, name
         _check_dlut(dl, dref)
+
+
+def test_paired_reductions_across_glyphs_of_different_n(S):
+    """The unstaged pass (uneven N, per-query glyph ids): lane pairs that straddle two glyphs of
+    different resolution (odd segment boundaries), glyph ids outside the pool, non-finite
+    directions and a ragged last warp.  dlut against the oracle over the valid queries; d/ddirs
+    NaN and the status bits set for the invalid ones."""
+    Ns, L = [4, 12, 31, 9], 4
+    luts = [O.bake_sh(n, L, I.sh_coeffs(1, L, 340 + k)[0] + np.eye(1, (L + 1) ** 2, 0)[0] * 2.0)
+            for k, n in enumerate(Ns)]
+    Lp, stored = upload_pool(S, luts)
+    counts = [101, 3, 2001, 777]
+    glyph = np.repeat(np.arange(4), counts).astype(np.int32)
+    Q = len(glyph)  # 2882: not a multiple of 32
+    rng = np.random.default_rng(341)
+    bad_id = rng.choice(Q, 40, replace=False)
+    glyph[bad_id[:20]] = -1
+    glyph[bad_id[20:]] = 4
+    dirs = I.directions(Q, 342)
+    bad_dir = rng.choice(np.setdiff1d(np.arange(Q), bad_id), 10, replace=False)
+    dirs[bad_dir[:5]] = np.nan
+    dirs[bad_dir[5:]] = 0.0
+    gR = rng.normal(size=Q).astype(np.float32)
+    gG = rng.normal(size=(Q, 3)).astype(np.float32)
+    dl = S.like_lut(Lp, zero=True)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dd = S.query_backward(Lp, _t(dirs), dl, gR=_t(gR), ggrad=_t(gG), glyph=_t(glyph), dev_status=st)
+    torch.cuda.synchronize()
+    assert st.item() & S.SHM_DEV_BOUNDS and st.item() & S.SHM_DEV_NONFINITE
+    ok = np.ones(Q, bool)
+    ok[bad_id] = False
+    ok[bad_dir] = False
+    off, Ns_ = O.make_pool(luts)[1:]
+    dref, ddref = O.query_vjp(stored.reshape(-1, 4), off, Ns_, dirs[ok], gR=gR[ok], gG=gG[ok], glyph=glyph[ok])
+    _check_dlut(dl.data.view(-1, 4).double().cpu().numpy(), dref)
+    ddn = dd.double().cpu().numpy()
+    assert np.isnan(ddn[~ok]).all() and np.isfinite(ddn[ok]).all()
