@@ -1124,11 +1124,27 @@ def planet_leg(args, S, torch):
     t_bin = timeit(lambda: P.query_random(P.out))
     t_dir = timeit(lambda: S.query(P.lut, P.dr, out=P.out), 3)
     t_coh = timeit(lambda: S.query(P.lut, P.dc, out=P.out), 3)
+    # the random half on 16-bit and cell-layout copies of the same table: speed against f32 texel
+    storage = {}
+    for name, dt, ly in (("f16_texel", S.SHM_F16, S.SHM_LAYOUT_TEXEL), ("bf16_texel", S.SHM_BF16, S.SHM_LAYOUT_TEXEL),
+                         ("f32_cell", S.SHM_F32, S.SHM_LAYOUT_CELL), ("f16_cell", S.SHM_F16, S.SHM_LAYOUT_CELL)):
+        t = S.like_lut(P.lut, dtype=dt, layout=ly)
+        S.pack_lut(P.lut, t)
+        ws = S.query_binned_workspace(t, P.Qr)
+        tb = timeit(lambda: S.query_binned(t, P.dr, ws, out=P.out), 3)
+        del ws
+        td = timeit(lambda: S.query(t, P.dr, out=P.out), 3)
+        storage[name] = {"table_MB": round(t.data.numel() * t.data.element_size() / 1e6, 1),
+                         "random_binned_ms": round(tb, 4), "binned_speedup_vs_f32_texel": round(t_bin / tb, 3),
+                         "random_direct_ms": round(td, 4), "direct_speedup_vs_f32_texel": round(t_dir / td, 3)}
+        del t
+        torch.cuda.empty_cache()
     res = {"workload": P.config["workload"], "random_queries": P.config["random_queries"],
            "l2_fetch_granularity_bytes": 64, "fbm_bake_ms": round(bake, 4),
            "random_binned": form(t_bin, P.Qr, ("binned", "query_random")),
            "random_direct": form(t_dir, P.Qr, ("direct", "planet_random_direct")),
            "coherent_direct": form(t_coh, P.Qc, ("direct", "query_coherent")),
+           "random_storage": storage,
            "step_ms": round(bake + t_bin + t_coh, 4),
            "step_queries_per_s": (P.Qr + P.Qc) / ((bake + t_bin + t_coh) * 1e-3),
            "note": "frac at 104 B/query = the paper's per-query bytes (4 corner records + direction + outputs, no "
