@@ -138,3 +138,31 @@ def test_build_backward_engines_agree_at_the_glyph_field_size(S):
     for r in [0, 1, 127, 128, 4095, 9999, G - 1]:
         oref = O.bake_sh_vjp(N, L, dl[r].double().cpu().numpy().reshape(6, N + 2, N + 2, 4))
         assert np.abs(tc1[r].double().cpu().numpy() - oref).max() <= 2e-5 * np.abs(oref).max(), r
+
+
+@pytest.mark.parametrize("per_sm", [63.9, 64, 100.5, 128, 131])
+def test_build_backward_glyph_group_sizing(S, per_sm):
+    """The tensor-core adjoint sizes its glyph groups from the SM count: below 64 glyphs per SM,
+    128-row groups with the texel sum split over cluster CTAs; from 64 per SM, groups of 64-128 rows
+    that fill whole waves of the SMs (the last group ragged), one wave up to 128 per SM and two above.
+    Every glyph against the float64 contraction of the same float32 operands (2e-5 of the largest
+    entry), and glyphs at group boundaries against the oracle's transpose of the bake."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    N, L = 7, 4
+    G = int(per_sm * sms)
+    T = 6 * (N + 2) ** 2
+    K = (L + 1) ** 2
+    g = torch.Generator(device="cuda").manual_seed(int(per_sm * 10))
+    D = S.alloc_lut(G, N)
+    D.data.copy_(torch.randn(D.data.numel(), device="cuda", generator=g))
+    basis = S.sh_basis(N, L)
+    dc = S.build_lut_backward(D, L, basis)
+    dl = D.data.view(G, T * 4)
+    ref = dl.double() @ basis[:K * T * 4].view(K, T * 4).double().T
+    assert float((dc.double() - ref).abs().max()) <= 2e-5 * float(ref.abs().max())
+    waves = -(-G // (128 * sms))
+    R = 128 if G < 64 * sms else -(-G // (waves * sms))
+    dcn = dc.double().cpu().numpy()
+    for r in sorted({0, R - 1, R, 2 * R - 1, G // 2, G - R, G - 1} & set(range(G))):
+        oref = O.bake_sh_vjp(N, L, dl[r].double().cpu().numpy().reshape(6, N + 2, N + 2, 4))
+        assert np.abs(dcn[r] - oref).max() <= 2e-5 * np.abs(oref).max(), r
