@@ -25,7 +25,9 @@ namespace {
 constexpr int N_SSHAPES = 3;
 constexpr int SSHAPES[N_SSHAPES] = {512, 1024, 256};
 
-template <int DT, int SBLOCK>
+// STD: the usual output set (R, gradient and normal; no chart derivatives, no cell indices), so the
+// per-query output checks drop out of the loop.
+template <int DT, int SBLOCK, bool STD>
 __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArgs a, uint32_t table_bytes)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -101,16 +103,16 @@ __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArg
                 Ru = (float)N * h.rs;
                 Rv = (float)N * h.rt;
                 grad = s2_gradient(c, Ru, Rv);
-                if (a.normal) nrm = surface_normal(d0, d1, d2, R, grad);
+                if (STD || a.normal) nrm = surface_normal(d0, d1, d2, R, grad);
                 f = c.f;
             } else {
                 status |= SHM_DEV_NONFINITE;
             }
-            if (a.R) __stcs(a.R + q, R);
-            if (a.grad) { __stcs(a.grad + 3 * q, grad.x); __stcs(a.grad + 3 * q + 1, grad.y); __stcs(a.grad + 3 * q + 2, grad.z); }
-            if (a.normal) { __stcs(a.normal + 3 * q, nrm.x); __stcs(a.normal + 3 * q + 1, nrm.y); __stcs(a.normal + 3 * q + 2, nrm.z); }
-            if (a.chart) { a.chart[2 * q] = Ru; a.chart[2 * q + 1] = Rv; }
-            if (a.fij) { a.fij[3 * q] = f; a.fij[3 * q + 1] = i; a.fij[3 * q + 2] = j; }
+            if (STD || a.R) __stcs(a.R + q, R);
+            if (STD || a.grad) { __stcs(a.grad + 3 * q, grad.x); __stcs(a.grad + 3 * q + 1, grad.y); __stcs(a.grad + 3 * q + 2, grad.z); }
+            if (STD || a.normal) { __stcs(a.normal + 3 * q, nrm.x); __stcs(a.normal + 3 * q + 1, nrm.y); __stcs(a.normal + 3 * q + 2, nrm.z); }
+            if (!STD && a.chart) { a.chart[2 * q] = Ru; a.chart[2 * q + 1] = Rv; }
+            if (!STD && a.fij) { a.fij[3 * q] = f; a.fij[3 * q + 1] = i; a.fij[3 * q + 2] = j; }
             d0 = n0; d1 = n1; d2 = n2;
         }
         __syncthreads();  // every read of this table is done before the next copy lands
@@ -118,21 +120,30 @@ __global__ void __launch_bounds__(SBLOCK, 1024 / SBLOCK) k_query_staged(QueryArg
     report_status(a.dev_status, status);
 }
 
-template <int DT, int SBLOCK>
-cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
+template <int DT, int SBLOCK, bool STD>
+cudaError_t launch_staged_o(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
 {
     const int smem = stage::TABLE_OFFSET + (int)table_bytes;
-    cudaError_t e = ensure_dynamic_smem((const void*)k_query_staged<DT, SBLOCK>, smem);
+    cudaError_t e = ensure_dynamic_smem((const void*)k_query_staged<DT, SBLOCK, STD>, smem);
     if (e != cudaSuccess) return e;
     int resident = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT, SBLOCK>, SBLOCK, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_query_staged<DT, SBLOCK, STD>, SBLOCK, smem) !=
+            cudaSuccess ||
         resident < 1)
         resident = 1;
     int64_t blocks = (int64_t)sm_count() * resident;
     if (blocks > a.L.n_glyphs) blocks = a.L.n_glyphs;
     if (blocks < 1) blocks = 1;
-    k_query_staged<DT, SBLOCK><<<(unsigned)blocks, SBLOCK, smem, s>>>(a, table_bytes);
+    k_query_staged<DT, SBLOCK, STD><<<(unsigned)blocks, SBLOCK, smem, s>>>(a, table_bytes);
     return cudaGetLastError();
+}
+
+template <int DT, int SBLOCK>
+cudaError_t launch_staged_t(const QueryArgs& a, uint32_t table_bytes, cudaStream_t s)
+{
+    const bool std_outputs = a.R && a.grad && a.normal && !a.chart && !a.fij;
+    return std_outputs ? launch_staged_o<DT, SBLOCK, true>(a, table_bytes, s)
+                       : launch_staged_o<DT, SBLOCK, false>(a, table_bytes, s);
 }
 
 template <int DT>
