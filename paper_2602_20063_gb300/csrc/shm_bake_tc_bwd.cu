@@ -7,8 +7,10 @@ namespace tc {
 // Adjoint of the bake on the tensor cores.  The bake is linear in the coefficients (Algorithm 1:
 // table = sum_k c_k basis_k), so its reverse mode is the transposed contraction
 //     dcoeffs[g][k] = sum_c dlut[g][c] basis[k][c]                     (c over the 4T table scalars)
-// with 128 glyphs on the MMA M side and the coefficients on N (K padded to Kp <= 128).  Operands:
-//   A = dlut tiles [128 glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
+// with a CTA's group of up to 128 glyphs on the MMA M side (rows beyond the group hold stale data and
+// are never stored; see plan() for the group size) and the coefficients on N (K padded to
+// Kp <= 128).  Operands:
+//   A = dlut tiles [R glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
 //       four converter warps into tf32 hi = x truncated (overwriting the raw tile) and
 //       lo = tf32_rna(x - hi);
 //   B = the transposed tf32 split of the basis, hiS / loS (part of shm_sh_basis's buffer), stored as
