@@ -62,13 +62,42 @@ __device__ __forceinline__ void corner_weights(const Herm2& A, const Herm2& B, f
         }
 }
 
+// Upstream values of query q read from global memory where bwd_query uses them (streaming loads).
+struct GlobalUp {
+    const BackwardArgs& a;
+    int64_t q;
+    __device__ __forceinline__ float gR() const { return __ldcs(a.gR + q); }
+    __device__ __forceinline__ float ggrad(int k) const { return __ldcs(a.ggrad + 3 * q + k); }
+    __device__ __forceinline__ float gnormal(int k) const { return __ldcs(a.gnormal + 3 * q + k); }
+    __device__ __forceinline__ float R_target() const { return __ldcs(a.R_target + q); }
+    __device__ __forceinline__ float n_target(int k) const { return __ldcs(a.n_target + 3 * q + k); }
+};
+
+// Upstream values loaded before the query's forward recompute (the arrays bwd_query reads: gR,
+// ggrad, gnormal; zero where absent), so that their latency overlaps it.
+struct PreUp {
+    float r, g0, g1, g2, n0, n1, n2;
+    __device__ __forceinline__ PreUp(const BackwardArgs& a, int64_t q)
+    {
+        r = a.gR ? __ldcs(a.gR + q) : 0.0f;
+        g0 = g1 = g2 = n0 = n1 = n2 = 0.0f;
+        if (a.ggrad) { g0 = __ldcs(a.ggrad + 3 * q); g1 = __ldcs(a.ggrad + 3 * q + 1); g2 = __ldcs(a.ggrad + 3 * q + 2); }
+        if (a.gnormal) { n0 = __ldcs(a.gnormal + 3 * q); n1 = __ldcs(a.gnormal + 3 * q + 1); n2 = __ldcs(a.gnormal + 3 * q + 2); }
+    }
+    __device__ __forceinline__ float gR() const { return r; }
+    __device__ __forceinline__ float ggrad(int k) const { return k == 0 ? g0 : (k == 1 ? g1 : g2); }
+    __device__ __forceinline__ float gnormal(int k) const { return k == 0 ? n0 : (k == 1 ? n1 : n2); }
+    __device__ __forceinline__ float R_target() const { return 0.0f; }  // not used without the fit loss
+    __device__ __forceinline__ float n_target(int) const { return 0.0f; }
+};
+
 // One query's reverse pass on glyph table Gr: the 2x2 footprint comes from `fetch(f, i, j)`;
 // `emit(rec, A, B, s, t, g_r, g_rs, g_rt)` receives the cell (record index of its corner (0,0)
 // within the glyph's texel table), the Hermite factors at (s, t) and the upstream values of
 // r, r_s, r_t, from which corner_weights gives the four record gradients; the direction gradient
-// goes to dd.
-template <bool FIT, class Fetch, class Emit>
-__device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, const GlyphRef& Gr, const Chart& c,
+// goes to dd.  `up` supplies the upstream values (GlobalUp or PreUp).
+template <bool FIT, class Up, class Fetch, class Emit>
+__device__ __forceinline__ void bwd_query(const BackwardArgs& a, const Up& up, const GlyphRef& Gr, const Chart& c,
                                           float d0, float d1, float d2, const Fetch& fetch, Emit& emit, float3& dd,
                                           float& loss_acc)
 {
@@ -117,13 +146,12 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
     const float iml = rsqrtf(ma * ma + mb * mb + mc * mc);
     const float na = ma * iml, nb = mb * iml, nc = mc * iml;
     // upstream in the (a, b, c) frame
-    float gRu_in = a.gR ? __ldcs(a.gR + q) : 0.0f;
+    float gRu_in = a.gR ? up.gR() : 0.0f;
     float gGa = 0.f, gGb = 0.f, gGc = 0.f, gna = 0.f, gnb = 0.f, gnc = 0.f;
     if (FIT) {
         // L_q = w_v (R - R_t)^2 + w_n |n - n_t|^2: upstream dL/dR, dL/dn in the frame
-        const float eR = R - __ldcs(a.R_target + q);
-        const float t0 = __ldcs(a.n_target + 3 * q), t1 = __ldcs(a.n_target + 3 * q + 1),
-                    t2 = __ldcs(a.n_target + 3 * q + 2);
+        const float eR = R - up.R_target();
+        const float t0 = up.n_target(0), t1 = up.n_target(1), t2 = up.n_target(2);
         const float ea = na - pick3(c.k, t0, t1, t2) * c.sigma, eb = nb - pick3(c.k1, t0, t1, t2),
                     ec = nc - pick3(c.k2, t0, t1, t2);
         loss_acc += a.w_value * eR * eR + a.w_normal * (ea * ea + eb * eb + ec * ec);
@@ -133,13 +161,13 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, int64_t q, cons
         gnc = 2.0f * a.w_normal * ec;
     }
     if (!FIT && a.ggrad) {
-        const float gx0 = __ldcs(a.ggrad + 3 * q), gx1 = __ldcs(a.ggrad + 3 * q + 1), gx2 = __ldcs(a.ggrad + 3 * q + 2);
+        const float gx0 = up.ggrad(0), gx1 = up.ggrad(1), gx2 = up.ggrad(2);
         gGa = pick3(c.k, gx0, gx1, gx2) * c.sigma;
         gGb = pick3(c.k1, gx0, gx1, gx2);
         gGc = pick3(c.k2, gx0, gx1, gx2);
     }
     if (!FIT && a.gnormal) {
-        const float gx0 = __ldcs(a.gnormal + 3 * q), gx1 = __ldcs(a.gnormal + 3 * q + 1), gx2 = __ldcs(a.gnormal + 3 * q + 2);
+        const float gx0 = up.gnormal(0), gx1 = up.gnormal(1), gx2 = up.gnormal(2);
         gna = pick3(c.k, gx0, gx1, gx2) * c.sigma;
         gnb = pick3(c.k1, gx0, gx1, gx2);
         gnc = pick3(c.k2, gx0, gx1, gx2);

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(BBLOCK, 4) k_query_bwd(BackwardArgs a)
                     sink.base = glyph_ref(a.D, gq).base;
                     sink.P = Gr.N + 2;
                     auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
-                    bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
                 }
                 if (a.ddirs) {
                     __stcs(a.ddirs + 3 * q, dd.x);
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(SBB, 2) k_query_bwd_staged(BackwardArgs a, uin
                 float3 dd = make_float3(qnan, qnan, qnan);
                 const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
                 Chart c;
-                if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, q, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
                 else status |= SHM_DEV_NONFINITE;
                 if (a.ddirs) { __stcs(a.ddirs + 3 * q, dd.x); __stcs(a.ddirs + 3 * q + 1, dd.y); __stcs(a.ddirs + 3 * q + 2, dd.z); }
             }

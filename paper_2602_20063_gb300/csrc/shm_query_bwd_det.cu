@@ -119,17 +119,30 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
         const GlyphRef Gr = glyph_ref(a.L, g);
         const int P = Gr.N + 2;
         float4* dbase = reinterpret_cast<float4*>(a.dlut) + glyph_ref(a.D, g).base;
+        // the next chunk's direction is loaded while this chunk computes, sorts and adds
+        float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;
+        if (s0 + tid < s1) {
+            n0 = __ldcs(a.dirs + 3 * (s0 + tid));
+            n1 = __ldcs(a.dirs + 3 * (s0 + tid) + 1);
+            n2 = __ldcs(a.dirs + 3 * (s0 + tid) + 2);
+        }
         for (int64_t c0 = s0; c0 < s1; c0 += DBLOCK) {
             // 1. reverse math per query; key and payload into shared memory
             const int64_t q = c0 + tid;
+            const float d0 = n0, d1 = n1, d2 = n2;
+            if (q + DBLOCK < s1) {
+                n0 = __ldcs(a.dirs + 3 * (q + DBLOCK));
+                n1 = __ldcs(a.dirs + 3 * (q + DBLOCK) + 1);
+                n2 = __ldcs(a.dirs + 3 * (q + DBLOCK) + 2);
+            }
             DetEmit<KT> emit{NO_KEY, pay, tid};
             if (q < s1) {
+                const PreUp up(a, q);  // issued before the chart, used after the forward recompute
                 float3 dd = make_float3(qnan, qnan, qnan);
-                const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
                 Chart c;
                 if (chart_of(d0, d1, d2, c)) {
                     auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
-                    bwd_query<false>(a, q, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
+                    bwd_query<false>(a, up, Gr, c, d0, d1, d2, fetch, emit, dd, loss_unused);
                 } else {
                     status |= SHM_DEV_NONFINITE;
                 }
