@@ -199,8 +199,14 @@ __global__ void __launch_bounds__(SBB, 2) k_query_bwd_staged(BackwardArgs a, uin
                 float3 dd = make_float3(qnan, qnan, qnan);
                 const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
                 Chart c;
-                if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
-                else status |= SHM_DEV_NONFINITE;
+                if constexpr (FIT) {
+                    if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    else status |= SHM_DEV_NONFINITE;
+                } else {
+                    const PreUp up(a, q);  // issued before the chart, used after the forward recompute
+                    if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, up, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    else status |= SHM_DEV_NONFINITE;
+                }
                 if (a.ddirs) { __stcs(a.ddirs + 3 * q, dd.x); __stcs(a.ddirs + 3 * q + 1, dd.y); __stcs(a.ddirs + 3 * q + 2, dd.z); }
             }
             paired_reds(reinterpret_cast<float4*>(a.dlut), sink, tid & 31);
