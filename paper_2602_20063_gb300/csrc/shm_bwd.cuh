@@ -91,6 +91,24 @@ struct PreUp {
     __device__ __forceinline__ float n_target(int) const { return 0.0f; }
 };
 
+// Fit targets loaded before the query's forward recompute (R_target, n_target), so that their
+// latency overlaps it.
+struct PreFit {
+    float rt, t0, t1, t2;
+    __device__ __forceinline__ PreFit(const BackwardArgs& a, int64_t q)
+    {
+        rt = __ldcs(a.R_target + q);
+        t0 = __ldcs(a.n_target + 3 * q);
+        t1 = __ldcs(a.n_target + 3 * q + 1);
+        t2 = __ldcs(a.n_target + 3 * q + 2);
+    }
+    __device__ __forceinline__ float gR() const { return 0.0f; }  // not used by the fit loss
+    __device__ __forceinline__ float ggrad(int) const { return 0.0f; }
+    __device__ __forceinline__ float gnormal(int) const { return 0.0f; }
+    __device__ __forceinline__ float R_target() const { return rt; }
+    __device__ __forceinline__ float n_target(int k) const { return k == 0 ? t0 : (k == 1 ? t1 : t2); }
+};
+
 // One query's reverse pass on glyph table Gr: the 2x2 footprint comes from `fetch(f, i, j)`;
 // `emit(rec, A, B, s, t, g_r, g_rs, g_rt)` receives the cell (record index of its corner (0,0)
 // within the glyph's texel table), the Hermite factors at (s, t) and the upstream values of

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(BBLOCK, 4) k_query_bwd(BackwardArgs a)
                     sink.base = glyph_ref(a.D, gq).base;
                     sink.P = Gr.N + 2;
                     auto fetch = [&a, &Gr](int f, int i, int j) { return fetch_corners<DT, LAYOUT>(a.L.data, Gr, f, i, j); };
-                    bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    if constexpr (FIT) bwd_query<FIT>(a, PreFit(a, q), Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    else bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
                 }
                 if (a.ddirs) {
                     __stcs(a.ddirs + 3 * q, dd.x);
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(SBB, 2) k_query_bwd_staged(BackwardArgs a, uin
                 const float d0 = __ldcs(a.dirs + 3 * q), d1 = __ldcs(a.dirs + 3 * q + 1), d2 = __ldcs(a.dirs + 3 * q + 2);
                 Chart c;
                 if constexpr (FIT) {
-                    if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, GlobalUp{a, q}, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
+                    const PreFit up(a, q);
+                    if (chart_of(d0, d1, d2, c)) bwd_query<FIT>(a, up, Gr, c, d0, d1, d2, fetch, sink, dd, loss_acc);
                     else status |= SHM_DEV_NONFINITE;
                 } else {
                     const PreUp up(a, q);  // issued before the chart, used after the forward recompute
