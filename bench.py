@@ -290,26 +290,51 @@ class GlyphField:
         self.S.query(self.lut, self.dirs_host, seg=self.seg, out=host_out)
 
     def e2e_step_pipeline(self, host_out):
-        """Public API from pinned host buffers, pipelined over glyph chunks on several streams: per
-        chunk H2D of its directions and coefficients, bake, query, D2H of its outputs, so that the
-        copy engines and the kernels of neighbouring chunks overlap."""
+        """Public API from pinned host buffers, pipelined over glyph chunks: each chunk's directions
+        and coefficients go host to device on one copy stream, its bake and query run on the kernel
+        stream, its outputs go device to host on a second copy stream.  Per-chunk events order a
+        chunk's copies and kernels, and each chunk buffer against the previous step's use of it, so
+        both copy directions and the kernels of neighbouring chunks (and steps) overlap."""
         torch, S = self.torch, self.S
-        main = torch.cuda.current_stream()
-        for st in self.e2e_streams:
-            st.wait_stream(main)
+        h2d, d2h = self.e2e_h2d, self.e2e_d2h
         for c, (lut_c, src_c, seg_c, g0, g1) in enumerate(self.e2e_chunks):
-            st = self.e2e_streams[c % len(self.e2e_streams)]
             q0, q1 = g0 * self.per, g1 * self.per
-            with torch.cuda.stream(st):
+            if self.e2e_used[c]:
+                h2d.wait_event(self.e2e_ev_q[c])  # the last query of this chunk has read its inputs
+            with torch.cuda.stream(h2d):
                 self.dirs[q0:q1].copy_(self.dirs_host[q0:q1], non_blocking=True)
                 self.coeffs[g0:g1].copy_(self.c_pinned[g0:g1], non_blocking=True)
-                S.build_lut(lut_c, src_c, ws=self.e2e_ws[c % len(self.e2e_streams)], stream=st)
-                out_c = {k: v[q0:q1] for k, v in self.out.items()}
-                S.query(lut_c, self.dirs[q0:q1], seg=seg_c, out=out_c, stream=st)
-                for k in ("R", "grad", "normal"):
-                    host_out[k][q0:q1].copy_(out_c[k], non_blocking=True)
-        for st in self.e2e_streams:
-            main.wait_stream(st)
+            self.e2e_ev_in[c].record(h2d)
+            k = c % len(self.e2e_streams)
+            ks = self.e2e_streams[k]
+            ks.wait_event(self.e2e_ev_in[c])
+            if self.e2e_used[c]:
+                ks.wait_event(self.e2e_ev_out[c])  # the last outputs of this chunk are on the host
+            S.build_lut(lut_c, src_c, ws=self.e2e_ws[k], stream=ks)
+            out_c = {kk: v[q0:q1] for kk, v in self.out.items()}
+            S.query(lut_c, self.dirs[q0:q1], seg=seg_c, out=out_c, stream=ks)
+            self.e2e_ev_q[c].record(ks)
+            d2h.wait_event(self.e2e_ev_q[c])
+            with torch.cuda.stream(d2h):
+                for kk in ("R", "grad", "normal"):
+                    host_out[kk][q0:q1].copy_(out_c[kk], non_blocking=True)
+            self.e2e_ev_out[c].record(d2h)
+            self.e2e_used[c] = True
+
+    def e2e_begin(self):
+        """Start of a timed window: the pipeline's streams wait for the current stream (its start
+        event and any earlier work on the buffers)."""
+        if self.e2e_mode == "copy_pipeline":
+            cur = self.torch.cuda.current_stream()
+            for st in [self.e2e_h2d, self.e2e_d2h] + self.e2e_streams:
+                st.wait_stream(cur)
+
+    def e2e_end(self):
+        """End of a timed window: the current stream waits for every copy and kernel of the pipeline."""
+        if self.e2e_mode == "copy_pipeline":
+            cur = self.torch.cuda.current_stream()
+            for st in [self.e2e_h2d, self.e2e_d2h] + self.e2e_streams:
+                cur.wait_stream(st)
 
     def e2e_setup(self, mode=None):
         self.e2e_mode = mode or self.e2e_mode_arg
@@ -320,8 +345,13 @@ class GlyphField:
         h2d = self.dirs.numel() * 4 + self.coeffs.numel() * 4
         d2h = sum(v.numel() * 4 for v in self.out.values())
         if self.e2e_mode == "zero_copy":
+            self.e2e_note = "kernels read the directions from and write the outputs to the page-locked host buffers"
             return host_out, h2d, d2h
+        self.e2e_note = (f"{chunks} glyph chunks: host-to-device copies on one stream, bake + query on {streams} kernel "
+                         "stream(s), device-to-host copies on a second copy stream, ordered by per-chunk events; "
+                         "consecutive steps overlap inside a timed window")
         self.e2e_streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.e2e_h2d, self.e2e_d2h = torch.cuda.Stream(), torch.cuda.Stream()
         per_glyph = S.records_per_glyph(self.N, self.layout) * S.record_bytes(self.dtype, self.layout)
         elem = self.lut.data.element_size()
         self.e2e_chunks = []
@@ -333,6 +363,9 @@ class GlyphField:
             src_c = S.Source(kind=S.SHM_SRC_SH, L=self.L, coeffs=self.coeffs[g0:g1], basis=self.basis)
             seg_c = (self.seg[g0:g1 + 1] - self.seg[g0]).contiguous()
             self.e2e_chunks.append((lut_c, src_c, seg_c, g0, g1))
+        n = len(self.e2e_chunks)
+        self.e2e_ev_in, self.e2e_ev_q, self.e2e_ev_out = ([torch.cuda.Event() for _ in range(n)] for _ in range(3))
+        self.e2e_used = [False] * n
         ws_c = self.e2e_chunks[0][1]
         self.e2e_ws = ([S.build_workspace(self.e2e_chunks[0][0], ws_c) for _ in range(streams)]
                        if self.engine == "tcgen05" else [None] * streams)
@@ -426,16 +459,20 @@ class GlyphField:
         keep = self.e2e_mode
         for mode in ("zero_copy", "copy_pipeline"):
             host_out, h2d, d2h = self.e2e_setup(mode)
+            self.e2e_begin()
             for _ in range(E2E_WARMUP):
                 self.e2e_step(host_out)
+            self.e2e_end()
             torch.cuda.synchronize()
             st = torch.cuda.current_stream()
             wins = []
             for _ in range(E2E_REPEATS):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(st)
+                self.e2e_begin()
                 for _ in range(E2E_STEPS):
                     self.e2e_step(host_out)
+                self.e2e_end()
                 e1.record(st)
                 torch.cuda.synchronize()
                 wins.append(e0.elapsed_time(e1) / E2E_STEPS)
@@ -1645,17 +1682,24 @@ def run_gpu(args):
 
     # ---- end to end through the public API from pinned host memory: E2E_WARMUP untimed steps, then
     # E2E_REPEATS windows of E2E_STEPS steps each (independent of --steps); the median window counts
+    # (a window's begin / end hooks let a pipelined step overlap the next one inside the window:
+    # the start event precedes every stream's first copy, the end event follows every last one)
     host_out, h2d, d2h = work.e2e_setup()
+    begin, end = getattr(work, "e2e_begin", lambda: None), getattr(work, "e2e_end", lambda: None)
+    begin()
     for _ in range(E2E_WARMUP):
         work.e2e_step(host_out)
+    end()
     torch.cuda.synchronize()
     n_e2e = getattr(work, "e2e_steps", E2E_STEPS)
     windows = []
     for _ in range(E2E_REPEATS):
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
+        begin()
         for _ in range(n_e2e):
             work.e2e_step(host_out)
+        end()
         a1.record(stream)
         torch.cuda.synchronize()
         windows.append(a0.elapsed_time(a1) / n_e2e)
@@ -1696,6 +1740,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                     "host_link_GBps": round((h2d + d2h) / (e2e_ms * 1e-3) / 1e9, 1),
                     "mode": getattr(work, "e2e_mode", "copies"),
+                    "pipeline": getattr(work, "e2e_note", None),
                     "timing": f"{E2E_WARMUP} warm-up steps, then the median of {E2E_REPEATS} windows of {n_e2e} steps "
                               f"(window ms per step: {', '.join(f'{w:.3f}' for w in windows)})",
                     "host_link_probe": link,
@@ -1733,7 +1778,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=16,
                     help="glyph field end to end: glyph chunks per step (copies and kernels of neighbouring chunks overlap)")
-    ap.add_argument("--e2e-streams", type=int, default=3, help="glyph field end to end: streams the chunks rotate over")
+    ap.add_argument("--e2e-streams", type=int, default=1,
+                    help="glyph field end to end: kernel streams the chunks rotate over (copies: one stream per direction)")
     ap.add_argument("--e2e-mode", choices=["zero_copy", "copy_pipeline"], default="copy_pipeline",
                     help="glyph field end to end: kernels on page-locked host buffers, or chunked copies")
     args = ap.parse_args(argv)
