@@ -14,11 +14,55 @@
 //   chart   x = d_k1/|d_k|, y = d_k2/|d_k|, s = (x+1)N/2 + 1/2 - i:  gd from gx + gs N/2, gy + gt N/2
 //   w = d/|d|                               gd += (gw - w (w.gw))/|d|
 // Face and cell indices are piecewise constant, so they carry no derivative.
+//
+// Where two independent lanes run the same operation the arithmetic is written on float2 pairs (the
+// t-interpolation of a quantity and of its s-derivative; the b and c components of a tangent-frame
+// vector; the corner weights' Hermite factors of s and t and the (x, y) and (z, w) halves of each
+// weight record): sm_100+ executes __ffma2_rn / __fmul2_rn / __fadd2_rn as one instruction for both
+// lanes, each lane rounded as the scalar operation, which frees issue slots in this
+// instruction-bound pass.  The forward's Hermite factors and s-rows stay scalar: paired, their
+// constant operands and pair alignment pushed the kernels past 64 registers into spills.
 #pragma once
 #include "shm_internal.h"
 
 namespace shm {
 
+// ------------------------------------------------------------------------------------------
+// Paired float32 arithmetic
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }  // a - b exactly rounded
+__device__ __forceinline__ float4 padd4(float4 a, float4 b)
+{
+    const float2 lo = padd(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 hi = padd(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Cubic Hermite factors (§3.3) at s (.x) and t (.y), with H0 = 1 - H1 used implicitly (difference
+// form), and their first derivatives (for the corner weights).
+struct Herm2P {
+    float2 H1, h0d, h1d, dH1, dh0d, dh1d;
+};
+
+__device__ __forceinline__ Herm2P herm2p(float2 u)
+{
+    Herm2P h;
+    const float2 u2 = pmul(u, u);
+    const float2 om = pfma(u, bc(-1.0f), bc(1.0f));  // 1 - u
+    const float2 uom = pmul(u, om);
+    h.H1 = pmul(u2, pfma(u, bc(-2.0f), bc(3.0f)));
+    h.h0d = pmul(uom, om);
+    h.h1d = pmul(u2, padd(u, bc(-1.0f)));
+    h.dH1 = pmul(bc(6.0f), uom);
+    h.dh0d = pmul(om, pfma(u, bc(-3.0f), bc(1.0f)));
+    h.dh1d = pmul(u, pfma(u, bc(3.0f), bc(-2.0f)));
+    return h;
+}
+
+// The same factors at one coordinate, with the second derivatives (the forward recompute).
 struct Herm2 {
     float H1, h0d, h1d, dH1, dh0d, dh1d, ddH1, ddh0d, ddh1d;
 };
@@ -40,26 +84,28 @@ __device__ __forceinline__ Herm2 herm2(float s)
 }
 
 // Weights of the four corner records (index bb * 2 + aa) for upstream (g_r, g_rs, g_rt) on the
-// value and its two chart derivatives: each record's (r, r_u h, r_v h, r_uv h^2) weights.
-__device__ __forceinline__ void corner_weights(const Herm2& A, const Herm2& B, float g_r, float g_rs, float g_rt,
-                                               float4 (&w)[4])
+// value and its two chart derivatives at (s, t): each record's (r, r_u h, r_v h, r_uv h^2) weights.
+__device__ __forceinline__ void corner_weights(float s, float t, float g_r, float g_rs, float g_rt, float4 (&w)[4])
 {
-    const float H0s = 1.0f - A.H1, dH0s = -A.dH1, H0t = 1.0f - B.H1, dH0t = -B.dH1;
-    const float al[2] = {g_r * H0s + g_rs * dH0s, g_r * A.H1 + g_rs * A.dH1};
-    const float ad[2] = {g_r * A.h0d + g_rs * A.dh0d, g_r * A.h1d + g_rs * A.dh1d};
-    const float be[2] = {g_rt * H0s, g_rt * A.H1}, bd[2] = {g_rt * A.h0d, g_rt * A.h1d};
-    const float Ht[2] = {H0t, B.H1}, dHt[2] = {dH0t, B.dH1}, hdt[2] = {B.h0d, B.h1d}, dhdt[2] = {B.dh0d, B.dh1d};
+    const Herm2P h = herm2p(make_float2(s, t));
+    const float2 H0 = pfma(h.H1, bc(-1.0f), bc(1.0f));  // (H0(s), H0(t))
+    // per corner column aa: (al, ad) weigh the record's (r, r_u h) rows against the t factors,
+    // (be, bd) against their t derivatives
+    const float2 AL0 = make_float2(fmaf(g_rs, -h.dH1.x, g_r * H0.x), fmaf(g_rs, h.dh0d.x, g_r * h.h0d.x));
+    const float2 AL1 = make_float2(fmaf(g_rs, h.dH1.x, g_r * h.H1.x), fmaf(g_rs, h.dh1d.x, g_r * h.h1d.x));
+    const float2 BE0 = pmul(bc(g_rt), make_float2(H0.x, h.h0d.x));
+    const float2 BE1 = pmul(bc(g_rt), make_float2(h.H1.x, h.h1d.x));
+    const float Ht[2] = {H0.y, h.H1.y}, dHt[2] = {-h.dH1.y, h.dH1.y};
+    const float hdt[2] = {h.h0d.y, h.h1d.y}, dhdt[2] = {h.dh0d.y, h.dh1d.y};
 #pragma unroll
-    for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-        for (int aa = 0; aa < 2; ++aa) {
-            float4 wv;
-            wv.x = al[aa] * Ht[bb] + be[aa] * dHt[bb];
-            wv.y = ad[aa] * Ht[bb] + bd[aa] * dHt[bb];
-            wv.z = al[aa] * hdt[bb] + be[aa] * dhdt[bb];
-            wv.w = ad[aa] * hdt[bb] + bd[aa] * dhdt[bb];
-            w[bb * 2 + aa] = wv;
-        }
+    for (int bb = 0; bb < 2; ++bb) {
+        const float2 x0 = pfma(BE0, bc(dHt[bb]), pmul(AL0, bc(Ht[bb])));
+        const float2 z0 = pfma(BE0, bc(dhdt[bb]), pmul(AL0, bc(hdt[bb])));
+        const float2 x1 = pfma(BE1, bc(dHt[bb]), pmul(AL1, bc(Ht[bb])));
+        const float2 z1 = pfma(BE1, bc(dhdt[bb]), pmul(AL1, bc(hdt[bb])));
+        w[bb * 2] = make_float4(x0.x, x0.y, z0.x, z0.y);
+        w[bb * 2 + 1] = make_float4(x1.x, x1.y, z1.x, z1.y);
+    }
 }
 
 // Upstream values of query q read from global memory where bwd_query uses them (streaming loads).
@@ -110,10 +156,10 @@ struct PreFit {
 };
 
 // One query's reverse pass on glyph table Gr: the 2x2 footprint comes from `fetch(f, i, j)`;
-// `emit(rec, A, B, s, t, g_r, g_rs, g_rt)` receives the cell (record index of its corner (0,0)
-// within the glyph's texel table), the Hermite factors at (s, t) and the upstream values of
-// r, r_s, r_t, from which corner_weights gives the four record gradients; the direction gradient
-// goes to dd.  `up` supplies the upstream values (GlobalUp or PreUp).
+// `emit(rec, s, t, g_r, g_rs, g_rt)` receives the cell (record index of its corner (0,0) within the
+// glyph's texel table), the cell coordinates and the upstream values of r, r_s, r_t, from which
+// corner_weights gives the four record gradients; the direction gradient goes to dd.  `up`
+// supplies the upstream values (GlobalUp, PreUp or PreFit).
 template <bool FIT, class Up, class Fetch, class Emit>
 __device__ __forceinline__ void bwd_query(const BackwardArgs& a, const Up& up, const GlyphRef& Gr, const Chart& c,
                                           float d0, float d1, float d2, const Fetch& fetch, Emit& emit, float3& dd,
@@ -141,85 +187,94 @@ __device__ __forceinline__ void bwd_query(const BackwardArgs& a, const Up& up, c
     const float pss1 = A.ddH1 * d1r + A.ddh0d * cr.c01.y + A.ddh1d * cr.c11.y;
     const float qss0 = A.ddH1 * e0 + A.ddh0d * cr.c00.w + A.ddh1d * cr.c10.w;
     const float qss1 = A.ddH1 * e1 + A.ddh0d * cr.c01.w + A.ddh1d * cr.c11.w;
-    const float dp = p1 - p0;
-    const float r = p0 + B.H1 * dp + B.h0d * q0 + B.h1d * q1;
-    const float rs = ps0 + B.H1 * (ps1 - ps0) + B.h0d * qs0 + B.h1d * qs1;
-    const float rt = B.dH1 * dp + B.dh0d * q0 + B.dh1d * q1;
+    // along t: (r, r_s) and (r_t, r_st) as pairs; r_ss and r_tt apart
+    const float2 P0 = make_float2(p0, ps0), Q0 = make_float2(q0, qs0), Q1 = make_float2(q1, qs1);
+    const float2 DP = psub(make_float2(p1, ps1), P0);
+    const float2 Rr = pfma(bc(B.h1d), Q1, pfma(bc(B.h0d), Q0, pfma(bc(B.H1), DP, P0)));  // (r, r_s)
+    const float2 Rt = pfma(bc(B.dh1d), Q1, pfma(bc(B.dh0d), Q0, pmul(bc(B.dH1), DP)));   // (r_t, r_st)
+    const float r = Rr.x, rs = Rr.y, rt = Rt.x, rst = Rt.y, dp = DP.x;
     const float rss = pss0 + B.H1 * (pss1 - pss0) + B.h0d * qss0 + B.h1d * qss1;
-    const float rst = B.dH1 * (ps1 - ps0) + B.dh0d * qs0 + B.dh1d * qs1;
     const float rtt = B.ddH1 * dp + B.ddh0d * q0 + B.ddh1d * q1;
     const float Nf = (float)N;
-    const float R = Gr.r0 + r, Ru = Nf * rs, Rv = Nf * rt;
+    const float R = Gr.r0 + r;
+    const float2 Ruv = pmul(bc(Nf), make_float2(rs, rt));  // (R_u, R_v) = tangent components (b, c) of V
     const float x = c.x, y = c.y;
+    const float2 xy = make_float2(x, y);
     const float rho2 = fmaf(x, x, fmaf(y, y, 1.0f));
     const float irho = rsqrtf(rho2), rho = rho2 * irho;  // reciprocal square root: no division below
-    // tangent-frame components (a, b, c) = (sigma e_k, e_k1, e_k2)
-    const float Va = -(x * Ru + y * Rv), Vb = Ru, Vc = Rv;
+    const float hr = 0.5f * rho;
+    // tangent-frame components (a, b, c) = (sigma e_k, e_k1, e_k2); (b, c) as pairs
+    const float Va = -(x * Ruv.x + y * Ruv.y);
     const float il = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-    const float wk = pick3(c.k, d0, d1, d2) * il * c.sigma;  // w . a
-    const float w1 = pick3(c.k1, d0, d1, d2) * il;            // w . b
-    const float w2 = pick3(c.k2, d0, d1, d2) * il;            // w . c
-    const float Ga = 0.5f * rho * Va, Gb = 0.5f * rho * Vb, Gc = 0.5f * rho * Vc;
-    const float ma = R * wk - Ga, mb = R * w1 - Gb, mc = R * w2 - Gc;
-    const float iml = rsqrtf(ma * ma + mb * mb + mc * mc);
-    const float na = ma * iml, nb = mb * iml, nc = mc * iml;
+    const float wk = pick3(c.k, d0, d1, d2) * il * c.sigma;                       // w . a
+    const float2 w12 = pmul(bc(il), make_float2(pick3(c.k1, d0, d1, d2), pick3(c.k2, d0, d1, d2)));  // w . b, w . c
+    const float Ga = hr * Va;
+    const float2 G12n = pmul(bc(-hr), Ruv);  // -(G_b, G_c)
+    const float ma = R * wk - Ga;
+    const float2 m12 = pfma(bc(R), w12, G12n);
+    const float iml = rsqrtf(ma * ma + m12.x * m12.x + m12.y * m12.y);
+    const float na = ma * iml;
+    const float2 n12 = pmul(bc(iml), m12);
     // upstream in the (a, b, c) frame
     float gRu_in = a.gR ? up.gR() : 0.0f;
-    float gGa = 0.f, gGb = 0.f, gGc = 0.f, gna = 0.f, gnb = 0.f, gnc = 0.f;
+    float gGa = 0.f, gna = 0.f;
+    float2 gG12 = make_float2(0.f, 0.f), gn12 = make_float2(0.f, 0.f);
     if (FIT) {
         // L_q = w_v (R - R_t)^2 + w_n |n - n_t|^2: upstream dL/dR, dL/dn in the frame
         const float eR = R - up.R_target();
         const float t0 = up.n_target(0), t1 = up.n_target(1), t2 = up.n_target(2);
-        const float ea = na - pick3(c.k, t0, t1, t2) * c.sigma, eb = nb - pick3(c.k1, t0, t1, t2),
-                    ec = nc - pick3(c.k2, t0, t1, t2);
-        loss_acc += a.w_value * eR * eR + a.w_normal * (ea * ea + eb * eb + ec * ec);
+        const float ea = na - pick3(c.k, t0, t1, t2) * c.sigma;
+        const float2 e12 = psub(n12, make_float2(pick3(c.k1, t0, t1, t2), pick3(c.k2, t0, t1, t2)));
+        loss_acc += a.w_value * eR * eR + a.w_normal * (ea * ea + e12.x * e12.x + e12.y * e12.y);
         gRu_in = 2.0f * a.w_value * eR;
-        gna = 2.0f * a.w_normal * ea;
-        gnb = 2.0f * a.w_normal * eb;
-        gnc = 2.0f * a.w_normal * ec;
+        const float wn2 = 2.0f * a.w_normal;
+        gna = wn2 * ea;
+        gn12 = pmul(bc(wn2), e12);
     }
     if (!FIT && a.ggrad) {
         const float gx0 = up.ggrad(0), gx1 = up.ggrad(1), gx2 = up.ggrad(2);
         gGa = pick3(c.k, gx0, gx1, gx2) * c.sigma;
-        gGb = pick3(c.k1, gx0, gx1, gx2);
-        gGc = pick3(c.k2, gx0, gx1, gx2);
+        gG12 = make_float2(pick3(c.k1, gx0, gx1, gx2), pick3(c.k2, gx0, gx1, gx2));
     }
     if (!FIT && a.gnormal) {
         const float gx0 = up.gnormal(0), gx1 = up.gnormal(1), gx2 = up.gnormal(2);
         gna = pick3(c.k, gx0, gx1, gx2) * c.sigma;
-        gnb = pick3(c.k1, gx0, gx1, gx2);
-        gnc = pick3(c.k2, gx0, gx1, gx2);
+        gn12 = make_float2(pick3(c.k1, gx0, gx1, gx2), pick3(c.k2, gx0, gx1, gx2));
     }
     // --- reverse
-    const float ndg = na * gna + nb * gnb + nc * gnc;
-    const float gma = (gna - na * ndg) * iml, gmb = (gnb - nb * ndg) * iml, gmc = (gnc - nc * ndg) * iml;
-    const float gRt = gRu_in + gma * wk + gmb * w1 + gmc * w2;
-    const float gwa = R * gma, gwb = R * gmb, gwc = R * gmc;
-    const float tGa = gGa - gma, tGb = gGb - gmb, tGc = gGc - gmc;
-    const float gVa = 0.5f * rho * tGa, gVb = 0.5f * rho * tGb, gVc = 0.5f * rho * tGc;
-    const float grho = 0.5f * (Va * tGa + Vb * tGb + Vc * tGc);
-    const float gRu = gVb - x * gVa;
-    const float gRv = gVc - y * gVa;
-    const float gx = -Ru * gVa + grho * x * irho;
-    const float gy = -Rv * gVa + grho * y * irho;
-    const float g_r = gRt, g_rs = Nf * gRu, g_rt = Nf * gRv;
+    const float ndg = na * gna + n12.x * gn12.x + n12.y * gn12.y;
+    const float gma = (gna - na * ndg) * iml;
+    const float2 gm12 = pmul(bc(iml), pfma(n12, bc(-ndg), gn12));
+    const float gRt = gRu_in + gma * wk + gm12.x * w12.x + gm12.y * w12.y;
+    const float gwa = R * gma;
+    const float2 gw12 = pmul(bc(R), gm12);
+    const float tGa = gGa - gma;
+    const float2 tG12 = psub(gG12, gm12);
+    const float gVa = hr * tGa;
+    const float2 gV12 = pmul(bc(hr), tG12);
+    const float grho = 0.5f * (Va * tGa + Ruv.x * tG12.x + Ruv.y * tG12.y);
+    const float2 gRuv = pfma(xy, bc(-gVa), gV12);                          // (gR_u, gR_v)
+    const float2 gxy = pfma(xy, bc(grho * irho), pmul(Ruv, bc(-gVa)));    // (gx, gy)
+    const float g_r = gRt;
+    const float2 g_st = pmul(bc(Nf), gRuv);                                // (g_rs, g_rt)
     // table: the cell's corner weights go to the emitter (record index of corner (0,0) within the
     // glyph's texel table; corner (aa, bb) is record rec + bb P + aa)
-    emit(((int64_t)c.f * (N + 2) + j) * (N + 2) + i, A, B, s, t, g_r, g_rs, g_rt);
+    emit(((int64_t)c.f * (N + 2) + j) * (N + 2) + i, s, t, g_r, g_st.x, g_st.y);
     if (a.ddirs) {
-        const float gs = g_r * rs + g_rs * rss + g_rt * rst;
-        const float gt = g_r * rt + g_rs * rst + g_rt * rtt;
-        const float gxx = gx + gs * 0.5f * Nf, gyy = gy + gt * 0.5f * Nf;
+        // (gs, gt) = g_r (r_s, r_t) + g_rs (r_ss, r_st) + g_rt (r_st, r_tt)
+        const float2 gst = pfma(bc(g_st.y), make_float2(rst, rtt),
+                                pfma(bc(g_st.x), make_float2(rss, rst), pmul(bc(g_r), make_float2(rs, rt))));
+        const float2 gxxyy = pfma(gst, bc(0.5f * Nf), gxy);
         // chart coordinates -> d (frame components; a-component carries sigma)
-        float dA = -(x * gxx + y * gyy) * c.im;  // along a = sigma e_k (c.im = 1/|d_k|)
-        float dB = gxx * c.im, dC = gyy * c.im;
+        float dA = -(x * gxxyy.x + y * gxxyy.y) * c.im;  // along a = sigma e_k (c.im = 1/|d_k|)
+        float2 dBC = pmul(gxxyy, bc(c.im));
         // w = d/|d|
-        const float wdg = wk * gwa + w1 * gwb + w2 * gwc;
+        const float wdg = wk * gwa + w12.x * gw12.x + w12.y * gw12.y;
         dA += (gwa - wk * wdg) * il;
-        dB += (gwb - w1 * wdg) * il;
-        dC += (gwc - w2 * wdg) * il;
+        dBC = pfma(pfma(w12, bc(-wdg), gw12), bc(il), dBC);
         // back to Cartesian (a = sigma e_k): component c.k gets dA sigma, c.k1 dB, c.k2 dC
         const float sA = dA * c.sigma;
+        const float dB = dBC.x, dC = dBC.y;
         dd = make_float3(c.k == 0 ? sA : (c.k1 == 0 ? dB : dC), c.k == 1 ? sA : (c.k1 == 1 ? dB : dC),
                          c.k == 2 ? sA : (c.k1 == 2 ? dB : dC));
     }

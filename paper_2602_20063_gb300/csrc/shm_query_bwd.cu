@@ -18,8 +18,7 @@ struct CaptureEmit {
     int P = 0;         // the glyph's padded table width
     int64_t rec = -1;  // record of corner (0,0) in the gradient table; -1: no contribution
     float s = 0.0f, t = 0.0f, g_r = 0.0f, g_rs = 0.0f, g_rt = 0.0f;
-    __device__ __forceinline__ void operator()(int64_t r, const Herm2&, const Herm2&, float s_, float t_, float gr,
-                                               float grs, float grt)
+    __device__ __forceinline__ void operator()(int64_t r, float s_, float t_, float gr, float grs, float grt)
     {
         rec = base + r;
         s = s_;
@@ -45,7 +44,7 @@ __device__ __forceinline__ void paired_reds(float4* dl, const CaptureEmit& e, in
 {
     float4 w[4];
     if (e.rec >= 0) {
-        corner_weights(herm2(e.s), herm2(e.t), e.g_r, e.g_rs, e.g_rt, w);
+        corner_weights(e.s, e.t, e.g_r, e.g_rs, e.g_rt, w);
     } else {
 #pragma unroll
         for (int m = 0; m < 4; ++m) w[m] = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -35,8 +35,7 @@ struct DetEmit {
     KT key;
     float* pay;  // [5][DBLOCK]: s, t, g_r, g_rs, g_rt
     int slot;
-    __device__ __forceinline__ void operator()(int64_t rec, const Herm2&, const Herm2&, float s, float t, float g_r,
-                                               float g_rs, float g_rt)
+    __device__ __forceinline__ void operator()(int64_t rec, float s, float t, float g_r, float g_rs, float g_rt)
     {
         key = ((KT)rec << DBITS) | (KT)slot;
         pay[slot] = s;
@@ -163,16 +162,11 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
                     const KT kr = key[r];
                     if (kr == NO_KEY || (kr >> DBITS) != cell) break;
                     const int src = (int)(kr & (DBLOCK - 1));
-                    const Herm2 A = herm2(pay[src]), B = herm2(pay[DBLOCK + src]);
                     float4 w[4];
-                    corner_weights(A, B, pay[2 * DBLOCK + src], pay[3 * DBLOCK + src], pay[4 * DBLOCK + src], w);
+                    corner_weights(pay[src], pay[DBLOCK + src], pay[2 * DBLOCK + src], pay[3 * DBLOCK + src],
+                                   pay[4 * DBLOCK + src], w);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        acc[m].x += w[m].x;
-                        acc[m].y += w[m].y;
-                        acc[m].z += w[m].z;
-                        acc[m].w += w[m].w;
-                    }
+                    for (int m = 0; m < 4; ++m) acc[m] = padd4(acc[m], w[m]);
                 }
             }
             // 4. one pass per corner: distinct cells touch distinct records within a pass
