@@ -1731,6 +1731,9 @@ def run_gpu(args):
                             " issue slots from unit counts x max clock" if dk.get("unit") == "T warp-inst/s" else
                             " FP32 SIMT from unit counts x max clock")}
     extras = {} if args.no_extras else work.extras(S, torch, args.steps)
+    if extras:
+        # the copy bandwidth behind every "frac_of_measured_hbm*" figure above, and where it came from
+        extras["hbm_peak_used"] = {"GBps": peaks["hbm_gbs"], "source": peaks["_source"]}
     line = {"metric": METRIC, "value": value, "unit": work.unit, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": ["f32", "f16", "bf16"][args.dtype_id], "data": "synthetic",

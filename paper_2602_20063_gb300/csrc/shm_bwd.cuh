@@ -27,20 +27,6 @@
 
 namespace shm {
 
-// ------------------------------------------------------------------------------------------
-// Paired float32 arithmetic
-__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }  // a - b exactly rounded
-__device__ __forceinline__ float4 padd4(float4 a, float4 b)
-{
-    const float2 lo = padd(make_float2(a.x, a.y), make_float2(b.x, b.y));
-    const float2 hi = padd(make_float2(a.z, a.w), make_float2(b.z, b.w));
-    return make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-
 // Cubic Hermite factors (§3.3) at s (.x) and t (.y), with H0 = 1 - H1 used implicitly (difference
 // form), and their first derivatives (for the corner weights).
 struct Herm2P {

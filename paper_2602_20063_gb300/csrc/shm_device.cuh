@@ -200,6 +200,22 @@ __device__ __forceinline__ Corners fetch_corners(const void* data, const GlyphRe
 }
 
 // ------------------------------------------------------------------------------------------
+// Paired float32 arithmetic (sm_100+): one instruction for the two lanes of a float2, each lane
+// rounded as the scalar operation (fma: one rounding).  Frees issue slots where two independent
+// lanes run the same operation; a broadcast operand (bc) costs nothing extra.
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }  // a - b, one rounding
+__device__ __forceinline__ float4 padd4(float4 a, float4 b)
+{
+    const float2 lo = padd(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 hi = padd(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// ------------------------------------------------------------------------------------------
 // 1-D cubic Hermite basis (§3.3) with H0 = 1 - H1 used implicitly (difference form)
 struct Herm {
     float H1, h0d, h1d;     // H1, H0d, H1d
@@ -224,26 +240,27 @@ struct HermOut {
     float r, rs, rt;  // value and d/ds, d/dt
 };
 
-// Tensor-product Hermite value and first derivatives from the four corner records.
+// Tensor-product Hermite value and first derivatives from the four corner records.  The rows along
+// s are formed as (value, d/ds) pairs and interpolated along t as pairs (paired float32 arithmetic,
+// the same operations in the same order as the scalar form).
 __device__ __forceinline__ HermOut hermite2(const Corners& c, float s, float t)
 {
     const Herm a = herm(s), b = herm(t);
-    // rows along s: value row p_b and v-derivative row q_b (Hermite of r_v h with r_uv h^2)
+    const float2 aH1 = make_float2(a.H1, a.dH1), ah0 = make_float2(a.h0d, a.dh0d), ah1 = make_float2(a.h1d, a.dh1d);
+    // rows along s: value row p_b and v-derivative row q_b (Hermite of r_v h with r_uv h^2), each
+    // with its s-derivative: P_b = (p_b, ps_b), Q_b = (q_b, qs_b)
     const float d0 = c.c10.x - c.c00.x, d1 = c.c11.x - c.c01.x;
     const float e0 = c.c10.z - c.c00.z, e1 = c.c11.z - c.c01.z;
-    const float p0 = c.c00.x + a.H1 * d0 + a.h0d * c.c00.y + a.h1d * c.c10.y;
-    const float p1 = c.c01.x + a.H1 * d1 + a.h0d * c.c01.y + a.h1d * c.c11.y;
-    const float q0 = c.c00.z + a.H1 * e0 + a.h0d * c.c00.w + a.h1d * c.c10.w;
-    const float q1 = c.c01.z + a.H1 * e1 + a.h0d * c.c01.w + a.h1d * c.c11.w;
-    const float ps0 = a.dH1 * d0 + a.dh0d * c.c00.y + a.dh1d * c.c10.y;
-    const float ps1 = a.dH1 * d1 + a.dh0d * c.c01.y + a.dh1d * c.c11.y;
-    const float qs0 = a.dH1 * e0 + a.dh0d * c.c00.w + a.dh1d * c.c10.w;
-    const float qs1 = a.dH1 * e1 + a.dh0d * c.c01.w + a.dh1d * c.c11.w;
+    const float2 P0 = pfma(ah1, bc(c.c10.y), pfma(ah0, bc(c.c00.y), pfma(aH1, bc(d0), make_float2(c.c00.x, 0.0f))));
+    const float2 P1 = pfma(ah1, bc(c.c11.y), pfma(ah0, bc(c.c01.y), pfma(aH1, bc(d1), make_float2(c.c01.x, 0.0f))));
+    const float2 Q0 = pfma(ah1, bc(c.c10.w), pfma(ah0, bc(c.c00.w), pfma(aH1, bc(e0), make_float2(c.c00.z, 0.0f))));
+    const float2 Q1 = pfma(ah1, bc(c.c11.w), pfma(ah0, bc(c.c01.w), pfma(aH1, bc(e1), make_float2(c.c01.z, 0.0f))));
+    const float2 DP = psub(P1, P0);
+    const float2 Rr = pfma(bc(b.h1d), Q1, pfma(bc(b.h0d), Q0, pfma(bc(b.H1), DP, P0)));  // (r, r_s)
     HermOut o;
-    const float dp = p1 - p0;
-    o.r = p0 + b.H1 * dp + b.h0d * q0 + b.h1d * q1;
-    o.rs = ps0 + b.H1 * (ps1 - ps0) + b.h0d * qs0 + b.h1d * qs1;
-    o.rt = b.dH1 * dp + b.dh0d * q0 + b.dh1d * q1;
+    o.r = Rr.x;
+    o.rs = Rr.y;
+    o.rt = b.dH1 * DP.x + b.dh0d * Q0.x + b.dh1d * Q1.x;
     return o;
 }
 
