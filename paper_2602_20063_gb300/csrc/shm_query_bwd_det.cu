@@ -9,9 +9,10 @@
 //   2. a bitonic sort of (cell, query) keys groups the chunk's queries by cell, in query order
 //      (keys in registers; partners within a warp by shuffles, across warps through shared memory);
 //   3. the first thread of each cell's run sums the corner weights of the run's queries in that order;
-//   4. four passes, one per corner (aa, bb), add those sums to the slab with plain loads and stores:
-//      within one pass distinct cells write distinct records, and the passes are separated by CTA
-//      barriers, so every record receives its contributions in a fixed order.
+//   4. four passes, one per corner (aa, bb), add those sums to the slab with one vector reduction
+//      (red.global.add.v4.f32) per cell: within one pass distinct cells reach distinct records, and
+//      the passes are separated by CTA barriers, so every record receives its contributions one at
+//      a time in a fixed order.
 // Chunks run in order inside the CTA, glyphs are disjoint, so the whole result is fixed.  Chunks of
 // 256 queries and four CTAs per SM (footprints read through L1/L2): with whole tables staged in
 // shared memory only two 1,024-thread CTAs fit per SM, which measured 5.7 ms against 4.7 ms on the
@@ -169,18 +170,13 @@ __global__ void __launch_bounds__(DBLOCK, DMINB) k_query_bwd_det(BackwardArgs a)
                     for (int m = 0; m < 4; ++m) acc[m] = padd4(acc[m], w[m]);
                 }
             }
-            // 4. one pass per corner: distinct cells touch distinct records within a pass
+            // 4. one pass per corner: distinct cells touch distinct records within a pass, so each
+            //    record receives at most one vector reduction per pass, and the CTA barrier between
+            //    passes orders a record's reductions from one pass before those of the next (the
+            //    same adds, in the same order, as a read-add-write, without waiting for the read)
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                if (head) {
-                    float4* p = dbase + (int64_t)cell + (m >> 1) * P + (m & 1);
-                    float4 v = *p;
-                    v.x += acc[m].x;
-                    v.y += acc[m].y;
-                    v.z += acc[m].z;
-                    v.w += acc[m].w;
-                    *p = v;
-                }
+                if (head) atomicAdd(dbase + (int64_t)cell + (m >> 1) * P + (m & 1), acc[m]);
                 __syncthreads();
             }
         }
