@@ -391,8 +391,8 @@ class GlyphField:
                               {"bound": "hbm", "algorithmic": lut_bytes + self.G * K * 4 + 4 * T * K * 4,
                                "unit": "GB/s", "peak": peaks["hbm_gbs"],
                                "per_unit": f"{lut_bytes / self.G:.0f} B of table written per glyph + coefficients + basis read "
-                                           f"(tensor work 3 x 2 K' x 4T = {3 * 2 * ((K + 31) // 32 * 32) * 4 * T / 1e6:.1f} MFLOP "
-                                           "tf32 per glyph is not the binding resource)",
+                                           f"(tensor work 3 x 2 K' x 4T = {3 * 2 * ((K + 7) // 8 * 8) * 4 * T / 1e6:.1f} MFLOP "
+                                           "tf32 per glyph, K' = K rounded up to the MMA's K step of 8, is not the binding resource)",
                                "files": ["paper_2602_20063_gb300/csrc/shm_bake_tc.cu"]}),
         }
         return terms

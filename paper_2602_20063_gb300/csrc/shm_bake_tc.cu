@@ -51,6 +51,7 @@ struct Args {
     int M;                // table columns, 4T
     int G;                // glyphs
     int Kp;               // padded K (multiple of 32)
+    int K;                // SH terms (K steps of 8 wholly beyond K are all zero and skipped)
     float* out;           // f32 texel table [G][M] when direct
     LutView view;         // output table (any dtype / layout) for the generic epilogue
     void* data;
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(256, 1)
                 const uint32_t bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
 #pragma unroll
                 for (int kk = 0; kk < KC / 8; ++kk) {
+                    if (c * KC + kk * 8 >= a.K) break;  // zero padding only (K >= 1: the first step always runs)
                     const uint32_t o = kk * 32;  // 8 tf32 = 32 B along K inside the 64-byte swizzle row
                     mma_tf32(d, sdesc(ah + o), sdesc(bh + o), (c | kk) != 0);
                     mma_tf32(d, sdesc(ah + o), sdesc(bl + o), 1);
@@ -363,6 +365,7 @@ cudaError_t launch_sh_build_tc(const LutView& out, void* data, int L, const floa
     a.M = M;
     a.G = G;
     a.Kp = Kp;
+    a.K = K;
     a.view = out;
     a.data = data;
     a.out = reinterpret_cast<float*>(data);

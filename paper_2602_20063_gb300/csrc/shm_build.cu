@@ -450,6 +450,22 @@ __device__ __forceinline__ float bump_sum(const BumpSmem& B, int nb, const Vec3&
     return sum;
 }
 
+// bump_sum at two sample directions at once: the same operations lane by lane (so the same sums),
+// with each bump's parameters read once and the arithmetic on float2 pairs (one instruction for
+// both samples); the two exp2 evaluations stay scalar.
+__device__ __forceinline__ float2 bump_sum2(const BumpSmem& B, int nb, const Vec3& wa, const Vec3& wb, float2 sum)
+{
+    const float2 wx = make_float2(wa.x, wb.x), wy = make_float2(wa.y, wb.y), wz = make_float2(wa.z, wb.z);
+#pragma unroll 4
+    for (int q = 0; q < nb; ++q) {
+        const float4 m = B.m[q];
+        const float2 dx = psub(wx, bc(m.x)), dy = psub(wy, bc(m.y)), dz = psub(wz, bc(m.z));
+        const float2 e = pmul(pfma(dz, dz, pfma(dy, dy, pmul(dx, dx))), bc(B.k[q]));
+        sum = pfma(bc(m.w), make_float2(ex2_approx(e.x), ex2_approx(e.y)), sum);
+    }
+    return sum;
+}
+
 // Value tables (SHM_LAYOUT_VALUE) of sampled sources: the table is the margin sample grid itself,
 // so 18 x 18 tiles of samples are evaluated and stored (plus the value offset), no differences.
 template <class Map>
@@ -668,7 +684,18 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
                 __syncthreads();
                 stage_bumps(bump, src, bc, nb);
                 __syncthreads();
-                for (int e = tid; e < Si * Sj; e += 256) Sf[e] = bump_sum(bump, nb, dir(i0 + e % Si, j0 + e / Si), Sf[e]);
+                // two samples per thread at a time (e and e + 256), the last odd one alone
+                for (int e = tid; e < Si * Sj; e += 512) {
+                    const int e2 = e + 256;
+                    if (e2 < Si * Sj) {
+                        const float2 v = bump_sum2(bump, nb, dir(i0 + e % Si, j0 + e / Si), dir(i0 + e2 % Si, j0 + e2 / Si),
+                                                   make_float2(Sf[e], Sf[e2]));
+                        Sf[e] = v.x;
+                        Sf[e2] = v.y;
+                    } else {
+                        Sf[e] = bump_sum(bump, nb, dir(i0 + e % Si, j0 + e / Si), Sf[e]);
+                    }
+                }
             }
         }
     }
