@@ -406,6 +406,42 @@ __device__ __forceinline__ float value_noise_box(float px, float py, float pz, c
     return e0 + wz * (e1 - e0);
 }
 
+// value_noise_box at two points at once (.x and .y): the same operations lane by lane (so the same
+// values), the fade and the trilinear interpolation on float2 pairs, the box corners per lane.
+__device__ __forceinline__ float2 quintic2(float2 t)
+{
+    return pmul(pmul(pmul(t, t), t), pfma(t, pfma(t, bc(6.0f), bc(-15.0f)), bc(10.0f)));
+}
+
+__device__ __forceinline__ float2 value_noise_box2(float2 px, float2 py, float2 pz, const float* T, int x0, int y0,
+                                                   int z0, int nx, int ny, int nz)
+{
+    const float2 fx = make_float2(floorf(px.x), floorf(px.y)), fy = make_float2(floorf(py.x), floorf(py.y));
+    const float2 fz = make_float2(floorf(pz.x), floorf(pz.y));
+    const float2 wx = quintic2(psub(px, fx)), wy = quintic2(psub(py, fy)), wz = quintic2(psub(pz, fz));
+    const int nxy = nx * ny;
+    const float* b[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int bx = min(max((int)(l ? fx.y : fx.x) - x0, 0), nx - 2);
+        const int by = min(max((int)(l ? fy.y : fy.x) - y0, 0), ny - 2);
+        const int bz = min(max((int)(l ? fz.y : fz.x) - z0, 0), nz - 2);
+        b[l] = T + bz * nxy + by * nx + bx;
+    }
+    float2 c[2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int o = dz * nxy + dy * nx;
+            const float2 v0 = make_float2(b[0][o], b[1][o]), v1 = make_float2(b[0][o + 1], b[1][o + 1]);
+            c[dz][dy] = pfma(wx, psub(v1, v0), v0);
+        }
+    const float2 e0 = pfma(wy, psub(c[0][1], c[0][0]), c[0][0]);
+    const float2 e1 = pfma(wy, psub(c[1][1], c[1][0]), c[1][0]);
+    return pfma(wz, psub(e1, e0), e0);
+}
+
 // ------------------------------------------------------------------------------------------
 // Sampled sources: value tables (k_value_build) and finite-difference records (k_fd_face).
 constexpr int FS = 18, MAX_BUMPS_SMEM = 128;
@@ -648,24 +684,52 @@ __global__ void __launch_bounds__(256) k_fd_face(LutView out, void* data, shm_so
             }
         }
         __syncthreads();
-        for (int e = tid; e < Si * Sj; e += 256) {
-            const Vec3 w = wdir(e % Si, e / Si);
-            float sum = 0.0f, freq = src.base_freq, amp = 1.0f;
-            for (int o = 0; o < src.octaves; ++o) {
-                const float px = w.x * freq, py = w.y * freq, pz = w.z * freq;
-                float v;
-                if (o < FBM_MAX_OCT && s_box[o][7]) {
-                    const int* bx = s_box[o];
-                    v = value_noise_box(px, py, pz, cache + bx[6], bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]);
-                } else {
-                    const uint32_t* key = src.keys + 3 * o;
-                    v = value_noise(px, py, pz, __ldg(key), __ldg(key + 1), __ldg(key + 2));
+        // two samples per thread at a time (e and e + 256), the last odd one alone: per octave the
+        // box parameters are read once for both and the cached lattice is interpolated on pairs
+        for (int e = tid; e < Si * Sj; e += 512) {
+            const int e2 = e + 256;
+            if (e2 < Si * Sj) {
+                const Vec3 wa = wdir(e % Si, e / Si), wb = wdir(e2 % Si, e2 / Si);
+                float2 sum = make_float2(0.0f, 0.0f);
+                float freq = src.base_freq, amp = 1.0f;
+                for (int o = 0; o < src.octaves; ++o) {
+                    const float2 px = pmul(make_float2(wa.x, wb.x), bc(freq));
+                    const float2 py = pmul(make_float2(wa.y, wb.y), bc(freq));
+                    const float2 pz = pmul(make_float2(wa.z, wb.z), bc(freq));
+                    float2 v;
+                    if (o < FBM_MAX_OCT && s_box[o][7]) {
+                        const int* bx = s_box[o];
+                        v = value_noise_box2(px, py, pz, cache + bx[6], bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]);
+                    } else {
+                        const uint32_t* key = src.keys + 3 * o;
+                        const uint32_t k0 = __ldg(key), k1 = __ldg(key + 1), k2 = __ldg(key + 2);
+                        v = make_float2(value_noise(px.x, py.x, pz.x, k0, k1, k2), value_noise(px.y, py.y, pz.y, k0, k1, k2));
+                    }
+                    sum = pfma(bc(amp), v, sum);
+                    freq *= src.lacunarity;
+                    amp *= src.gain;
                 }
-                sum = fmaf(amp, v, sum);
-                freq *= src.lacunarity;
-                amp *= src.gain;
+                Sf[e] = src.amplitude * sum.x;
+                Sf[e2] = src.amplitude * sum.y;
+            } else {
+                const Vec3 w = wdir(e % Si, e / Si);
+                float sum = 0.0f, freq = src.base_freq, amp = 1.0f;
+                for (int o = 0; o < src.octaves; ++o) {
+                    const float px = w.x * freq, py = w.y * freq, pz = w.z * freq;
+                    float v;
+                    if (o < FBM_MAX_OCT && s_box[o][7]) {
+                        const int* bx = s_box[o];
+                        v = value_noise_box(px, py, pz, cache + bx[6], bx[0], bx[1], bx[2], bx[3], bx[4], bx[5]);
+                    } else {
+                        const uint32_t* key = src.keys + 3 * o;
+                        v = value_noise(px, py, pz, __ldg(key), __ldg(key + 1), __ldg(key + 2));
+                    }
+                    sum = fmaf(amp, v, sum);
+                    freq *= src.lacunarity;
+                    amp *= src.gain;
+                }
+                Sf[e] = src.amplitude * sum;
             }
-            Sf[e] = src.amplitude * sum;
         }
     } else {
         __shared__ BumpSmem bump;
