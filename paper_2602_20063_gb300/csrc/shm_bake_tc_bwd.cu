@@ -36,7 +36,7 @@ namespace tc {
 // the cluster's ranks in rank order through distributed shared memory, so the result does not
 // depend on timing (deterministic, no atomics, no workspace).
 //   warp 0 lane 0: TMA producer   warp 1: TMEM allocation, lane 0 issues the MMAs
-//   warps 4-7: drain (TMEM lane quadrant = warp % 4) and epilogue   warps 8-11: tf32 split
+//   warps 4-7: drain (TMEM lane quadrant = warp % 4) and epilogue   warps 2-3, 8-11: tf32 split
 // Every mbarrier wait is bounded (1 s) and raises SHM_DEV_TIMEOUT on expiry; the cluster barriers
 // are reached by every thread of every CTA the same number of times, aborted or not.
 namespace bwd {
@@ -48,6 +48,7 @@ constexpr int CH = 16;                        // stages per TMEM chunk
 constexpr int PFW = 16;                       // stages per L2 prefetch box (256 c: 1 KB of each glyph row)
 constexpr int PFA = 2;                        // prefetch boxes ahead of the shared-memory loads
 constexpr int THREADS = 384;
+constexpr int SPLIT_T = 192;                  // tf32-split threads: warps 2-3 and 8-11
 constexpr uint32_t STAGE_CAP = 196 * 1024;    // shared memory for the stages (and the partials after them)
 constexpr uint32_t BAR_BYTES = 1024;
 constexpr int MAXSTAGE = 8;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int st = 0; st < a.nstage; ++st) {
             mbar_init(full0 + 8 * st, 1);
-            mbar_init(conv0 + 8 * st, 128);
+            mbar_init(conv0 + 8 * st, SPLIT_T);
             mbar_init(empty0 + 8 * st, 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -242,9 +243,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < DRAIN_LIMIT_NS) {
             }
         }
-    } else if (warp >= 8) {
+    } else if (warp >= 8 || warp == 2 || warp == 3) {
         // ---------------------------------------------------------------- tf32 split of each stage
-        const int t = threadIdx.x - 256;
+        const int t = warp >= 8 ? threadIdx.x - 256 : threadIdx.x + 64;  // warps 8-11: 0-127, warps 2-3: 128-191
         constexpr int n4 = (int)(A_TILE / 16);
         for (int it = 0; it < nst; ++it) {
             const int st = it % a.nstage;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             float4* hi = reinterpret_cast<float4*>(stA(st));
             float4* lo = reinterpret_cast<float4*>(stAlo(st));
 #pragma unroll
-            for (int i = t; i < n4; i += 128) {
+            for (int i = t; i < n4; i += SPLIT_T) {
                 const float4 x = hi[i];
                 float4 h, l;
                 h.x = tf32_trunc(x.x); h.y = tf32_trunc(x.y); h.z = tf32_trunc(x.z); h.w = tf32_trunc(x.w);
