@@ -11,7 +11,7 @@ namespace tc {
 // are never stored; see plan() for the group size) and the coefficients on N (K padded to
 // Kp <= 128).  Operands:
 //   A = dlut tiles [R glyphs x 16 c], loaded raw by TMA (64-byte swizzle) and split in place by
-//       four converter warps into tf32 hi = x truncated (overwriting the raw tile) and
+//       six converter warps into tf32 hi = x truncated (overwriting the raw tile) and
 //       lo = tf32_rna(x - hi);
 //   B = the transposed tf32 split of the basis, hiS / loS (part of shm_sh_basis's buffer), stored as
 //       one contiguous [Kp][16 c] slab per stage with its rows already in the 64-byte swizzled order
@@ -22,7 +22,7 @@ namespace tc {
 // [0, Kp) take A_hi B_hi and [Kp, 2 Kp) A_hi B_lo, and A_lo B_hi adds into [0, Kp); the drain warps
 // add both halves (TMEM: two buffers of 2 Kp columns).  Two MMA instructions instead of three per
 // K step at the same tensor work: 0.962 -> 0.870 ms on the glyph field, the MMA issuer being one of
-// the two roles that set the pace.
+// the two roles that set the pace; the split, the other, runs on six warps (0.870 -> 0.853 ms).
 // Accuracy: the error of the tensor cores' float32 accumulation grew with the length of the sum
 // kept in one TMEM accumulator (measured: 4.6e-5 of the largest entry after 434 stages, against
 // 7.9e-6 for a plain float32 sum).  So the MMAs accumulate CH stages at a time into one of two
