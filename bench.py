@@ -1524,8 +1524,9 @@ class Fit:
                                  "per_unit": "12 B direction + 16 B targets + 64 B table reads per query, plus the "
                                              "gradient table read-modify-written once (atomics hit L2)",
                                  "files": ["paper_2602_20063_gb300/csrc/shm_query_bwd.cu"]},
-            "adam": {"bound": "hbm", "algorithmic": tab * 7, "unit": "GB/s", "peak": peaks["hbm_gbs"],
-                     "per_unit": "param, grad, m, v read + param, m, v, grad written: 28 B per scalar",
+            "adam": {"bound": "hbm", "algorithmic": tab * 8, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                     "per_unit": "param, grad, m, v read + param, m, v written + grad zeroed for the next step: "
+                                 "32 B per scalar",
                      "files": ["paper_2602_20063_gb300/csrc/shm_query_bwd.cu"]},
         }
 
