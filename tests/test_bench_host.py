@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that the GPU numbers rest on: the whole-job rate, the traffic
-lookup keyed by the kernel's source hash, the clock record, and the argument defaults."""
+lookup keyed by the kernel's source hash, the clock record, the argument defaults, and the event
+ordering of the glyph field's end-to-end copy pipeline."""
 import importlib.util
 import json
 import os
@@ -71,3 +72,125 @@ def test_defaults_are_one_gpu_and_a_short_run(bench):
     a = bench.parse_args([])
     assert a.gpus == 1 and a.warmup >= 3 and a.workload == "glyphs" and a.impl == "shm"
     assert a.dtype_id == 0 and a.layout_id == 0
+
+
+class _Graph:
+    """Stream-ordered operations with event dependencies, as the bench's pipeline issues them."""
+
+    def __init__(self):
+        self.ops, self.edges, self.last, self.records = [], {}, {}, {}
+        self.current = None
+
+    def add(self, stream, what):
+        i = len(self.ops)
+        self.ops.append((stream, what))
+        self.edges[i] = set()
+        if stream in self.last:
+            self.edges[self.last[stream]].add(i)
+        self.last[stream] = i
+        return i
+
+    def after(self, x, y):
+        """True if op x is ordered after op y."""
+        seen, todo = set(), [y]
+        while todo:
+            n = todo.pop()
+            for m in self.edges[n]:
+                if m == x:
+                    return True
+                if m not in seen:
+                    seen.add(m)
+                    todo.append(m)
+        return False
+
+
+def test_e2e_pipeline_orders_every_chunk_buffer(bench):
+    """The glyph field's end-to-end step, replayed with recording streams and events over two
+    steps: a chunk's bake and query follow its host-to-device copy; its outputs go back after its
+    query; and in the next step its directions are overwritten only after the previous query read
+    them, its outputs only after the previous device-to-host copy read them."""
+    import contextlib
+    g = _Graph()
+
+    class Stream:
+        def __init__(self, name):
+            self.name = name
+
+        def wait_event(self, ev):
+            i = g.add(self.name, ("wait", ev.name))
+            g.edges[g.records[(ev.name, ev.version)]].add(i)
+
+    class Event:
+        def __init__(self, name):
+            self.name, self.version = name, 0
+
+        def record(self, stream):
+            self.version += 1
+            g.records[(self.name, self.version)] = g.add(stream.name, ("record", self.name))
+
+    class View:
+        def __init__(self, name, lo, hi):
+            self.name, self.lo, self.hi = name, lo, hi
+
+        def copy_(self, src, non_blocking=False):
+            g.add(g.current, ("copy", self.name, src.name, self.lo))
+
+    class Tensor:
+        def __init__(self, name):
+            self.name = name
+
+        def __getitem__(self, sl):
+            return View(self.name, sl.start, sl.stop)
+
+    class Cuda:
+        @staticmethod
+        @contextlib.contextmanager
+        def stream(s):
+            prev, g.current = g.current, s.name
+            yield
+            g.current = prev
+
+    class Torch:
+        cuda = Cuda
+
+    class Lib:
+        @staticmethod
+        def build_lut(lut, src, ws=None, stream=None):
+            g.add(stream.name, ("bake", lut))
+
+        @staticmethod
+        def query(lut, dirs, seg=None, out=None, stream=None):
+            g.add(stream.name, ("query", lut))
+
+    C = 4
+    w = bench.GlyphField.__new__(bench.GlyphField)
+    w.torch, w.S, w.per = Torch, Lib, 2
+    w.e2e_h2d, w.e2e_d2h, w.e2e_streams = Stream("h2d"), Stream("d2h"), [Stream("kernels")]
+    w.e2e_chunks = [(c, None, None, 3 * c, 3 * c + 3) for c in range(C)]
+    w.e2e_ws = [None]
+    w.dirs, w.dirs_host, w.coeffs, w.c_pinned = Tensor("dirs"), Tensor("dirs_host"), Tensor("coeffs"), Tensor("c_host")
+    w.out = {k: Tensor("out_" + k) for k in ("R", "grad", "normal")}
+    w.e2e_ev_in, w.e2e_ev_q, w.e2e_ev_out = ([Event(f"{n}{c}") for c in range(C)] for n in ("in", "q", "out"))
+    w.e2e_used = [False] * C
+    host_out = {k: Tensor("host_" + k) for k in ("R", "grad", "normal")}
+    for _ in range(2):
+        w.e2e_step_pipeline(host_out)
+
+    def find(kind, step, match):
+        """The step-th op of this kind whose fields match ({position: value})."""
+        hits = [i for i, (s, what) in enumerate(g.ops) if what[0] == kind and
+                all(what[j] == v for j, v in match.items())]
+        return hits[step]
+
+    for c in range(C):
+        q0 = 3 * c * w.per
+        for step in range(2):
+            h2d = find("copy", step, {1: "dirs", 3: q0})
+            bake, query = find("bake", step, {1: c}), find("query", step, {1: c})
+            back = [find("copy", step, {1: "host_" + k, 3: q0}) for k in ("R", "grad", "normal")]
+            assert g.after(bake, h2d) and g.after(query, bake)
+            assert all(g.after(b, query) for b in back)
+            if step == 1:
+                assert g.after(h2d, find("query", 0, {1: c}))  # directions read by the last query
+                assert all(g.after(query, find("copy", 0, {1: "host_" + k, 3: q0}))
+                           for k in ("R", "grad", "normal"))  # outputs read by the last copy back
